@@ -1,0 +1,140 @@
+"""CPU oracle for the DFR sort path.  TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs of
+``bench.py`` may import this package.  It shares no code with the CUDA path,
+and the CUDA path never falls back to it.
+
+The arithmetic lives in ``oracle.c``: a plain least-significant-digit radix
+sort made of counting sorts (8-bit digits, every pass run, stable), following
+the paper's Preliminaries (count / convert counts to indices / deal) and its
+LSD radix sort (Algorithm 1).  This module only compiles that file with gcc
+and marshals numpy arrays to it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (plain gcc, -O2)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def load_library(path: str):
+    """Load a compiled oracle library and declare its signatures."""
+    lib = ctypes.CDLL(path)
+    u64 = ctypes.c_uint64
+    p = ctypes.c_void_p
+    for name, args in (
+        ("oracle_sort_u32", [p, u64]),
+        ("oracle_sort_u64", [p, u64]),
+        ("oracle_sort_u64_kv", [p, p, u64]),
+        ("oracle_sort_u32_kv", [p, p, u64]),
+        ("oracle_counting_pass_u32", [p, p, u64, ctypes.c_int]),
+    ):
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    return lib
+
+
+def _get():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = load_library(build())
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _check(rc: int) -> None:
+    if rc != 0:
+        raise RuntimeError("oracle failed with code %d" % rc)
+
+
+class Oracle:
+    """numpy front end over one compiled oracle library (the real one by
+    default; tests may pass a deliberately broken build to check the pins)."""
+
+    def __init__(self, lib=None):
+        self.lib = lib if lib is not None else _get()
+
+    def sort_u32(self, keys) -> np.ndarray:
+        k = np.array(keys, dtype=np.uint32, copy=True, order="C")
+        _check(self.lib.oracle_sort_u32(_ptr(k), k.size))
+        return k
+
+    def sort_u64(self, keys) -> np.ndarray:
+        k = np.array(keys, dtype=np.uint64, copy=True, order="C")
+        _check(self.lib.oracle_sort_u64(_ptr(k), k.size))
+        return k
+
+    def sort_u64_kv(self, keys, vals):
+        k = np.array(keys, dtype=np.uint64, copy=True, order="C")
+        v = np.array(vals, dtype=np.uint32, copy=True, order="C")
+        if k.size != v.size:
+            raise ValueError("keys and vals differ in length")
+        _check(self.lib.oracle_sort_u64_kv(_ptr(k), _ptr(v), k.size))
+        return k, v
+
+    def sort_u32_kv(self, keys, vals):
+        k = np.array(keys, dtype=np.uint32, copy=True, order="C")
+        v = np.array(vals, dtype=np.uint32, copy=True, order="C")
+        if k.size != v.size:
+            raise ValueError("keys and vals differ in length")
+        _check(self.lib.oracle_sort_u32_kv(_ptr(k), _ptr(v), k.size))
+        return k, v
+
+    def counting_pass_u32(self, keys, shift: int) -> np.ndarray:
+        src = np.array(keys, dtype=np.uint32, copy=True, order="C")
+        dst = np.empty_like(src)
+        _check(self.lib.oracle_counting_pass_u32(_ptr(src), _ptr(dst), src.size, int(shift)))
+        return dst
+
+
+_default = None
+
+
+def default() -> Oracle:
+    global _default
+    if _default is None:
+        _default = Oracle()
+    return _default
+
+
+def sort_u32(keys):
+    return default().sort_u32(keys)
+
+
+def sort_u64(keys):
+    return default().sort_u64(keys)
+
+
+def sort_u64_kv(keys, vals):
+    return default().sort_u64_kv(keys, vals)
+
+
+def sort_u32_kv(keys, vals):
+    return default().sort_u32_kv(keys, vals)
+
+
+def counting_pass_u32(keys, shift: int):
+    return default().counting_pass_u32(keys, shift)

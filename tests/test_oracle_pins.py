@@ -1,0 +1,176 @@
+"""Pins for the CPU oracle, against things other than itself (CPU only).
+
+The oracle computes the stable ascending order of unsigned keys (payloads move
+with their keys).  That result is unique for a given input, so it is pinned by:
+  * brute force: a stable insertion sort (the paper's small-bucket diversion,
+    Section "MSD Radix Sorts") on every array up to length 6 over alphabets that
+    differ in each byte position and include the extreme values;
+  * a library routine: numpy's stable sort / stable argsort on random inputs;
+  * the invariants of a sort: output nondecreasing, output a permutation of
+    the input (exact multiset histogram), and for key-value input the payload
+    (original index) points back at its key and rises inside every run of
+    equal keys (stability);
+  * special cases with closed-form answers: all-equal, already sorted,
+    reverse-sorted distinct keys.
+A companion test (test_oracle_mutants.py) checks that plausible mistakes in
+oracle.c are caught by these pins.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+U32_ALPHABET = [0, 0x1, 0x100, 0x10000, 0x1000000, 0xFFFFFFFF]
+U64_ALPHABET = [0, 0x1, 0x100, 0x100000000, 0x100000000000000, 0x8000000000000000, 0xFFFFFFFFFFFFFFFF]
+
+
+def insertion_sort_pairs(keys):
+    """Stable insertion sort of (key, original index) pairs, by key only."""
+    recs = [(int(k), i) for i, k in enumerate(keys)]
+    for i in range(1, len(recs)):
+        cur = recs[i]
+        j = i - 1
+        while j >= 0 and recs[j][0] > cur[0]:
+            recs[j + 1] = recs[j]
+            j -= 1
+        recs[j + 1] = cur
+    return [r[0] for r in recs], [r[1] for r in recs]
+
+
+def check_sorted_permutation(inp, out):
+    inp = np.asarray(inp)
+    out = np.asarray(out)
+    assert out.shape == inp.shape
+    if out.size > 1:
+        assert np.all(out[1:] >= out[:-1]), "not nondecreasing"
+    vi, ci = np.unique(inp, return_counts=True)
+    vo, co = np.unique(out, return_counts=True)
+    assert np.array_equal(vi, vo) and np.array_equal(ci, co), "not a permutation of the input"
+
+
+def check_kv_stable(kin, kout, vout):
+    kin = np.asarray(kin)
+    kout = np.asarray(kout)
+    vout = np.asarray(vout).astype(np.int64)
+    n = kin.size
+    assert np.array_equal(np.sort(vout), np.arange(n)), "payloads are not a permutation"
+    assert np.array_equal(kin[vout], kout), "payload does not point back at its key"
+    if n > 1:
+        same = kout[1:] == kout[:-1]
+        assert np.all(vout[1:][same] > vout[:-1][same]), "equal keys out of input order"
+
+
+@pytest.mark.parametrize("n", range(0, 7))
+def test_u32_exhaustive_vs_insertion_sort(n):
+    orc = oracle.default()
+    for tup in itertools.product(U32_ALPHABET, repeat=n):
+        want, _ = insertion_sort_pairs(tup)
+        got = orc.sort_u32(np.array(tup, dtype=np.uint32))
+        assert got.tolist() == want, tup
+
+
+@pytest.mark.parametrize("n", range(0, 6))
+def test_u64_exhaustive_vs_insertion_sort(n):
+    orc = oracle.default()
+    for tup in itertools.product(U64_ALPHABET, repeat=n):
+        want, _ = insertion_sort_pairs(tup)
+        got = orc.sort_u64(np.array(tup, dtype=np.uint64))
+        assert got.tolist() == want, tup
+
+
+@pytest.mark.parametrize("n", range(0, 6))
+def test_u64_kv_exhaustive_vs_insertion_sort(n):
+    orc = oracle.default()
+    alpha = U64_ALPHABET[:5]
+    for tup in itertools.product(alpha, repeat=n):
+        want_k, want_v = insertion_sort_pairs(tup)
+        k, v = orc.sort_u64_kv(np.array(tup, dtype=np.uint64), np.arange(n, dtype=np.uint32))
+        assert k.tolist() == want_k and v.tolist() == want_v, tup
+
+
+@pytest.mark.parametrize("n", range(0, 6))
+def test_u32_kv_exhaustive_vs_insertion_sort(n):
+    orc = oracle.default()
+    alpha = U32_ALPHABET[:5]
+    for tup in itertools.product(alpha, repeat=n):
+        want_k, want_v = insertion_sort_pairs(tup)
+        k, v = orc.sort_u32_kv(np.array(tup, dtype=np.uint32), np.arange(n, dtype=np.uint32))
+        assert k.tolist() == want_k and v.tolist() == want_v, tup
+
+
+def test_random_small_vs_numpy_stable():
+    orc = oracle.default()
+    g = np.random.Generator(np.random.PCG64(synth.BASE_SEED))
+    for trial in range(1500):
+        n = int(g.integers(0, 2001))
+        bits = int(g.integers(1, 33))
+        k32 = g.integers(0, 1 << bits, size=n, dtype=np.uint64).astype(np.uint32)
+        assert np.array_equal(orc.sort_u32(k32), np.sort(k32, kind="stable"))
+        bits64 = int(g.integers(1, 65))
+        k64 = g.bit_generator.random_raw(n).astype(np.uint64) >> np.uint64(64 - bits64)
+        assert np.array_equal(orc.sort_u64(k64), np.sort(k64, kind="stable"))
+        v = np.arange(n, dtype=np.uint32)
+        kk, vv = orc.sort_u64_kv(k64, v)
+        order = np.argsort(k64, kind="stable")
+        assert np.array_equal(kk, k64[order]) and np.array_equal(vv, v[order])
+        kk, vv = orc.sort_u32_kv(k32, v)
+        order = np.argsort(k32, kind="stable")
+        assert np.array_equal(kk, k32[order]) and np.array_equal(vv, v[order])
+
+
+@pytest.mark.parametrize("dist", synth.U32_DISTRIBUTIONS)
+def test_u32_invariants_medium(dist):
+    n = (1 << 20) + 12345
+    a = synth.u32(dist, n, synth.BASE_SEED + 20)
+    out = oracle.sort_u32(a)
+    check_sorted_permutation(a, out)
+    assert np.array_equal(out, np.sort(a, kind="stable"))
+
+
+@pytest.mark.parametrize("dist", synth.U64_DISTRIBUTIONS)
+def test_u64_kv_invariants_medium(dist):
+    n = (1 << 19) + 777
+    k = synth.u64(dist, n, synth.BASE_SEED + 30)
+    v = synth.index_payload(n)
+    ko, vo = oracle.sort_u64_kv(k, v)
+    check_sorted_permutation(k, ko)
+    check_kv_stable(k, ko, vo)
+    assert np.array_equal(oracle.sort_u64(k), ko)
+
+
+def test_special_cases():
+    n = 100003
+    eq = np.full(n, 0xDEADBEEF, dtype=np.uint32)
+    assert np.array_equal(oracle.sort_u32(eq), eq)
+    srt = synth.sorted_u32(n, 5)
+    assert np.array_equal(oracle.sort_u32(srt), srt)
+    distinct = np.unique(synth.uniform_u32(n, 6))
+    assert np.array_equal(oracle.sort_u32(distinct[::-1].copy()), distinct)
+    eq64 = np.full(n, 0xFEDCBA9876543210, dtype=np.uint64)
+    k, v = oracle.sort_u64_kv(eq64, np.arange(n, dtype=np.uint32))
+    assert np.array_equal(k, eq64) and np.array_equal(v, np.arange(n, dtype=np.uint32))
+    d64 = np.unique(synth.uniform64_u64(n, 7))
+    k, v = oracle.sort_u64_kv(d64[::-1].copy(), np.arange(d64.size, dtype=np.uint32))
+    assert np.array_equal(k, d64)
+    assert np.array_equal(v, np.arange(d64.size, dtype=np.uint32)[::-1])
+
+
+@pytest.mark.parametrize("shift", [0, 3, 8, 13, 16, 24])
+def test_counting_pass_is_stable_partition(shift):
+    """One counting sort on one digit (Preliminaries): records come out grouped
+    by digit in ascending digit order, each group in input order -- exactly a
+    stable argsort of the digit (library routine)."""
+    a = synth.uniform_u32(50021, 11 + shift)
+    out = oracle.counting_pass_u32(a, shift)
+    digit = (a >> np.uint32(shift)) & np.uint32(255)
+    assert np.array_equal(out, a[np.argsort(digit, kind="stable")])
+
+
+def test_empty_and_single():
+    assert oracle.sort_u32(np.empty(0, np.uint32)).size == 0
+    assert oracle.sort_u64(np.array([7], np.uint64)).tolist() == [7]
+    k, v = oracle.sort_u64_kv(np.empty(0, np.uint64), np.empty(0, np.uint32))
+    assert k.size == 0 and v.size == 0
