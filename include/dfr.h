@@ -1,0 +1,198 @@
+/*
+ * dfr.h -- C ABI of the GB300 (sm_103a) Diverting Fast Radix sort library.
+ *
+ * The library sorts unsigned integer keys (optionally with 32-bit payloads)
+ * ascending and STABLY, with the hot path of the paper's Diverting Fast Radix
+ * method: a recursive most-significant-digit radix partition (count, convert
+ * the counts into indices, deal; Preliminaries and Section "Most Significant
+ * Digit (MSD) Radix Sorts"), where every bucket below a size threshold is
+ * diverted to a different, stable small-bucket sort (Algorithm 2 and Section
+ * "Analysis", the diversion threshold N_d) and buckets holding one repeated
+ * key are left alone (Section MSD: last-digit buckets hold equal keys).
+ *
+ * Conventions shared by every call:
+ *   - Pointers to keys, payloads, scratch buffers and workspace are DEVICE
+ *     pointers owned by the caller (allocate them however you like, e.g. with
+ *     PyTorch).  The library allocates no device memory in these calls.
+ *   - Every sort call is asynchronous on `stream` (0 = legacy default stream):
+ *     it only enqueues kernels and returns.  Device-side failures are recorded
+ *     in a status word inside the workspace; read them with
+ *     dfr_last_device_status().
+ *   - The result lands in place in `keys` (and `vals`).  `buf`/`vbuf` are the
+ *     paper's extra buffer of the input's size (Section MSD: "a suitably sized
+ *     extra buffer"); their contents are undefined afterwards.
+ *   - n == 0 and n == 1 return DFR_OK without touching the GPU.
+ *   - A single array may hold at most DFR_MAX_N keys.
+ *   - Ranges [keys, keys+n) and [buf, buf+n) (and the payload pair) must not
+ *     overlap; overlap returns DFR_ERR_INVALID_ARG.
+ *   - The workspace must be at least dfr_workspace_bytes() bytes and 256-byte
+ *     aligned.  One workspace serves one call at a time: calls sharing a
+ *     workspace must be ordered on one stream (or otherwise serialised).
+ *
+ * Return codes: DFR_OK on success, otherwise one of the DFR_ERR_* values;
+ * a call that returns an error enqueues nothing.
+ */
+#ifndef DFR_H
+#define DFR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; declared here so this header needs no CUDA
+ * include. */
+typedef struct CUstream_st* dfr_stream_t;
+
+enum dfr_status {
+    DFR_OK = 0,
+    DFR_ERR_INVALID_ARG = 1,  /* null pointer, overlap, n too large, misaligned workspace */
+    DFR_ERR_WORKSPACE = 2,    /* workspace smaller than required, or a device queue overflowed */
+    DFR_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    DFR_ERR_TIMEOUT = 4,      /* a device-side wait gave up after its iteration limit */
+    DFR_ERR_OVER_BUDGET = 5,  /* a served request exceeds the server's memory budget */
+    DFR_ERR_BUSY = 6,         /* the server cannot take the request now */
+    DFR_ERR_BOUNDS = 7        /* a device-side bounds check rejected a write (result invalid) */
+};
+
+enum dfr_key_type {
+    DFR_U32 = 0,     /* uint32 keys */
+    DFR_U64 = 1,     /* uint64 keys */
+    DFR_U64_KV = 2,  /* uint64 keys with uint32 payloads */
+    DFR_U32_KV = 3   /* uint32 keys with uint32 payloads */
+};
+
+/* Largest number of keys in one array (the decoupled look-back keeps 30-bit
+ * counts per digit). */
+#define DFR_MAX_N ((uint64_t)((1u << 30) - 1u))
+
+/*
+ * dfr_workspace_bytes -- bytes of device workspace one sort of n keys of
+ * `key_type` needs.  Pure host arithmetic, no CUDA call.
+ * Errors: DFR_ERR_INVALID_ARG for an unknown key type, n > DFR_MAX_N or a
+ * null `bytes`.
+ */
+int dfr_workspace_bytes(int key_type, uint64_t n, size_t* bytes);
+
+/*
+ * dfr_sort_u32 -- sort n uint32 keys ascending in place (the whole DFR path:
+ * count, prefix, deal per level; divert small buckets; leave constant buckets).
+ *   keys  [n] device, in/out
+ *   buf   [n] device scratch (the extra buffer of Algorithm 2)
+ *   ws    device workspace of ws_bytes >= dfr_workspace_bytes(DFR_U32, n)
+ */
+int dfr_sort_u32(uint32_t* keys, uint32_t* buf, uint64_t n, void* ws, size_t ws_bytes,
+                 dfr_stream_t stream);
+
+/* dfr_sort_u64 -- as dfr_sort_u32 for uint64 keys (DFR_U64 workspace). */
+int dfr_sort_u64(uint64_t* keys, uint64_t* buf, uint64_t n, void* ws, size_t ws_bytes,
+                 dfr_stream_t stream);
+
+/*
+ * dfr_sort_u64_kv -- stable sort of (uint64 key, uint32 payload) records by
+ * key: each payload moves with its key and equal keys keep their input order
+ * (Section MSD: stable with an extra buffer and a stable diversion).
+ *   keys/vals [n] device in/out;  kbuf/vbuf [n] device scratch.
+ */
+int dfr_sort_u64_kv(uint64_t* keys, uint32_t* vals, uint64_t* kbuf, uint32_t* vbuf, uint64_t n,
+                    void* ws, size_t ws_bytes, dfr_stream_t stream);
+
+/* dfr_sort_u32_kv -- as dfr_sort_u64_kv for uint32 keys (DFR_U32_KV workspace). */
+int dfr_sort_u32_kv(uint32_t* keys, uint32_t* vals, uint32_t* kbuf, uint32_t* vbuf, uint64_t n,
+                    void* ws, size_t ws_bytes, dfr_stream_t stream);
+
+/*
+ * dfr_last_device_status -- wait for `stream`, then report the device status
+ * word of the last call that used `ws`: DFR_OK, DFR_ERR_TIMEOUT,
+ * DFR_ERR_BOUNDS or DFR_ERR_WORKSPACE (queue capacity), in *status.
+ * Returns DFR_ERR_CUDA if the copy or the synchronisation fails.
+ */
+int dfr_last_device_status(const void* ws, dfr_stream_t stream, int* status);
+
+/* Per-call counters, filled from the workspace by dfr_get_stats(). */
+#define DFR_STATS_MAX_LEVELS 16
+typedef struct {
+    uint64_t n_total;                                  /* keys in the call (all arrays) */
+    uint32_t key_bytes, val_bytes;                     /* w and v */
+    uint32_t levels;                                   /* partition levels that did work */
+    uint32_t device_status;                            /* as dfr_last_device_status */
+    uint64_t level_segments[DFR_STATS_MAX_LEVELS];     /* large segments partitioned per level */
+    uint64_t level_tiles[DFR_STATS_MAX_LEVELS];        /* tiles per level */
+    uint64_t level_keys[DFR_STATS_MAX_LEVELS];         /* keys dealt per level */
+    uint64_t level_hist_keys[DFR_STATS_MAX_LEVELS];    /* keys re-read by a per-level count */
+    uint64_t cta_buckets, cta_keys;                    /* diverted to the CTA shared-memory sort */
+    uint64_t tiny_buckets, tiny_keys;                  /* diverted to the warp sort */
+    uint64_t const_buckets, const_keys;                /* constant buckets left alone */
+    uint64_t copy_keys;                                /* constant keys moved back from buf */
+    uint64_t model_bytes;                              /* minimal bytes of the executed plan */
+} dfr_stats_t;
+
+/* dfr_get_stats -- wait for `stream` and copy the counters of the last call
+ * that used `ws` into *out.  DFR_ERR_CUDA on a failed copy. */
+int dfr_get_stats(const void* ws, dfr_stream_t stream, dfr_stats_t* out);
+
+/* ---------------------------------------------------------------- batch -- */
+
+/* One array of a batch.  All arrays of one batch call share `key_type`. */
+typedef struct {
+    int key_type;   /* DFR_U32, DFR_U64, DFR_U64_KV or DFR_U32_KV */
+    void* keys;     /* [n] device, in/out */
+    void* vals;     /* [n] device payloads (kv types only, else NULL) */
+    void* kbuf;     /* [n] device scratch for keys */
+    void* vbuf;     /* [n] device scratch for payloads (kv types only) */
+    uint64_t n;
+} dfr_segment_t;
+
+/*
+ * dfr_batch_workspace_bytes -- workspace bytes for one dfr_sort_batch call
+ * over `count` arrays (host array `segs`).  No CUDA call.
+ */
+int dfr_batch_workspace_bytes(const dfr_segment_t* segs, uint32_t count, size_t* bytes);
+
+/*
+ * dfr_sort_batch -- sort `count` independent arrays with one launch sequence:
+ * every kernel is persistent and pulls tiles and buckets of all arrays from
+ * device work queues, so thousands of uneven arrays cost the same number of
+ * launches as one.  Each array's result is exactly that of sorting it alone.
+ * The descriptor table is copied to the device before the call returns, so
+ * `segs` may be reused at once.
+ * Errors: DFR_ERR_INVALID_ARG for mixed key types, null pointers, overlap or
+ * an array above DFR_MAX_N; DFR_ERR_WORKSPACE for a short workspace.
+ */
+int dfr_sort_batch(const dfr_segment_t* segs, uint32_t count, void* ws, size_t ws_bytes,
+                   dfr_stream_t stream);
+
+/* ---------------------------------------------------- debug and profiling -- */
+
+/*
+ * dfr_set_debug -- process-wide debug knobs (not for production use).
+ *   spin_limit     iterations a device-side wait may spin before it gives up
+ *                  and records DFR_ERR_TIMEOUT (0 = default limit);
+ *   force_timeout  1 = the decoupled look-back waits on a status word that no
+ *                  tile ever sets, so it must time out (tests the timeout path
+ *                  without hanging anything); 0 = normal.
+ */
+int dfr_set_debug(uint32_t spin_limit, int force_timeout);
+
+/* dfr_profile_enable -- 1: record CUDA events around every kernel launch of
+ * later calls (per kernel kind), 0: stop.  dfr_profile_read() waits for the
+ * device, returns per-kind totals and clears them.  Kinds are listed by
+ * dfr_profile_kind_name(). */
+int dfr_profile_enable(int on);
+#define DFR_PROFILE_KINDS 10
+int dfr_profile_read(double* ms_total /*[DFR_PROFILE_KINDS]*/, uint64_t* launches /*[DFR_PROFILE_KINDS]*/);
+const char* dfr_profile_kind_name(int kind);
+
+/* dfr_launch_count -- kernels this process has launched through the library. */
+uint64_t dfr_launch_count(void);
+
+/* dfr_status_string -- short text for a status code. */
+const char* dfr_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFR_H */

@@ -1,0 +1,296 @@
+"""Python binding of libdfr.so, the GB300 Diverting Fast Radix sort library.
+
+Argument marshalling only: every function below has the name of the C entry
+point it forwards to (include/dfr.h) and passes raw device pointers, lengths
+and a CUDA stream.  Pointers may be given as ints or as torch tensors (their
+data_ptr() is used); streams as ints, torch.cuda.Stream objects or None (the
+current torch stream).  PyTorch is only used for device memory and streams.
+
+There is no fallback: if libdfr.so has not been built, importing works but
+the first call raises, naming the build step.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdfr.so")
+
+DFR_OK = 0
+DFR_ERR_INVALID_ARG = 1
+DFR_ERR_WORKSPACE = 2
+DFR_ERR_CUDA = 3
+DFR_ERR_TIMEOUT = 4
+DFR_ERR_OVER_BUDGET = 5
+DFR_ERR_BUSY = 6
+DFR_ERR_BOUNDS = 7
+
+DFR_U32 = 0
+DFR_U64 = 1
+DFR_U64_KV = 2
+DFR_U32_KV = 3
+
+DFR_MAX_N = (1 << 30) - 1
+DFR_PROFILE_KINDS = 10
+DFR_STATS_MAX_LEVELS = 16
+
+KEY_BYTES = {DFR_U32: 4, DFR_U64: 8, DFR_U64_KV: 8, DFR_U32_KV: 4}
+HAS_VALS = {DFR_U32: False, DFR_U64: False, DFR_U64_KV: True, DFR_U32_KV: True}
+
+
+class DfrError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__("%s: %s (code %d)" % (what or "dfr", _status_text(code), code))
+
+
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+
+
+class dfr_segment_t(ctypes.Structure):
+    _fields_ = [("key_type", ctypes.c_int), ("keys", _vp), ("vals", _vp), ("kbuf", _vp), ("vbuf", _vp),
+                ("n", _u64)]
+
+
+class dfr_stats_t(ctypes.Structure):
+    _fields_ = [("n_total", _u64), ("key_bytes", _u32), ("val_bytes", _u32), ("levels", _u32),
+                ("device_status", _u32),
+                ("level_segments", _u64 * DFR_STATS_MAX_LEVELS), ("level_tiles", _u64 * DFR_STATS_MAX_LEVELS),
+                ("level_keys", _u64 * DFR_STATS_MAX_LEVELS), ("level_hist_keys", _u64 * DFR_STATS_MAX_LEVELS),
+                ("cta_buckets", _u64), ("cta_keys", _u64), ("tiny_buckets", _u64), ("tiny_keys", _u64),
+                ("const_buckets", _u64), ("const_keys", _u64), ("copy_keys", _u64), ("model_bytes", _u64)]
+
+
+_SIGNATURES = {
+    "dfr_workspace_bytes": (ctypes.c_int, [ctypes.c_int, _u64, ctypes.POINTER(_sz)]),
+    "dfr_sort_u32": (ctypes.c_int, [_vp, _vp, _u64, _vp, _sz, _vp]),
+    "dfr_sort_u64": (ctypes.c_int, [_vp, _vp, _u64, _vp, _sz, _vp]),
+    "dfr_sort_u64_kv": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp]),
+    "dfr_sort_u32_kv": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp]),
+    "dfr_last_device_status": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_int)]),
+    "dfr_get_stats": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(dfr_stats_t)]),
+    "dfr_batch_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(dfr_segment_t), _u32, ctypes.POINTER(_sz)]),
+    "dfr_sort_batch": (ctypes.c_int, [ctypes.POINTER(dfr_segment_t), _u32, _vp, _sz, _vp]),
+    "dfr_set_debug": (ctypes.c_int, [_u32, ctypes.c_int]),
+    "dfr_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "dfr_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64)]),
+    "dfr_profile_kind_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "dfr_launch_count": (_u64, []),
+    "dfr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Load libdfr.so (built by paper_2207_14334_gb300.build.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libdfr.so is not built (run __graft_entry__.build() or "
+                                   "python -m paper_2207_14334_gb300.build); there is no CPU fallback")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _status_text(code: int) -> str:
+    try:
+        return load().dfr_status_string(int(code)).decode()
+    except Exception:  # library missing: still describe the code
+        return {0: "ok"}.get(code, "error")
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(s) -> int:
+    if s is None:
+        import torch
+
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def check(rc: int, what: str = "") -> None:
+    """Raise DfrError for a non-zero status."""
+    if rc != DFR_OK:
+        raise DfrError(rc, what)
+
+
+# ----------------------------------------------------------- C entry points
+
+def dfr_workspace_bytes(key_type: int, n: int) -> int:
+    out = _sz(0)
+    check(load().dfr_workspace_bytes(int(key_type), int(n), ctypes.byref(out)), "dfr_workspace_bytes")
+    return int(out.value)
+
+
+def dfr_sort_u32(keys, buf, n, ws, ws_bytes, stream=None) -> int:
+    return load().dfr_sort_u32(_ptr(keys), _ptr(buf), int(n), _ptr(ws), int(ws_bytes), _stream(stream))
+
+
+def dfr_sort_u64(keys, buf, n, ws, ws_bytes, stream=None) -> int:
+    return load().dfr_sort_u64(_ptr(keys), _ptr(buf), int(n), _ptr(ws), int(ws_bytes), _stream(stream))
+
+
+def dfr_sort_u64_kv(keys, vals, kbuf, vbuf, n, ws, ws_bytes, stream=None) -> int:
+    return load().dfr_sort_u64_kv(_ptr(keys), _ptr(vals), _ptr(kbuf), _ptr(vbuf), int(n), _ptr(ws),
+                                  int(ws_bytes), _stream(stream))
+
+
+def dfr_sort_u32_kv(keys, vals, kbuf, vbuf, n, ws, ws_bytes, stream=None) -> int:
+    return load().dfr_sort_u32_kv(_ptr(keys), _ptr(vals), _ptr(kbuf), _ptr(vbuf), int(n), _ptr(ws),
+                                  int(ws_bytes), _stream(stream))
+
+
+def dfr_last_device_status(ws, stream=None) -> int:
+    st = ctypes.c_int(0)
+    check(load().dfr_last_device_status(_ptr(ws), _stream(stream), ctypes.byref(st)), "dfr_last_device_status")
+    return int(st.value)
+
+
+def dfr_get_stats(ws, stream=None) -> dict:
+    s = dfr_stats_t()
+    check(load().dfr_get_stats(_ptr(ws), _stream(stream), ctypes.byref(s)), "dfr_get_stats")
+    out = {}
+    for name, _ in dfr_stats_t._fields_:
+        v = getattr(s, name)
+        out[name] = list(v) if hasattr(v, "__len__") else int(v)
+    return out
+
+
+def _segments(segs):
+    arr = (dfr_segment_t * len(segs))()
+    for i, s in enumerate(segs):
+        if isinstance(s, dict):
+            arr[i] = dfr_segment_t(int(s["key_type"]), _ptr(s.get("keys")), _ptr(s.get("vals")),
+                                   _ptr(s.get("kbuf")), _ptr(s.get("vbuf")), int(s["n"]))
+        else:
+            kt, keys, vals, kbuf, vbuf, n = s
+            arr[i] = dfr_segment_t(int(kt), _ptr(keys), _ptr(vals), _ptr(kbuf), _ptr(vbuf), int(n))
+    return arr
+
+
+def dfr_batch_workspace_bytes(segs) -> int:
+    arr = _segments(segs)
+    out = _sz(0)
+    check(load().dfr_batch_workspace_bytes(arr, len(segs), ctypes.byref(out)), "dfr_batch_workspace_bytes")
+    return int(out.value)
+
+
+def dfr_sort_batch(segs, ws, ws_bytes, stream=None) -> int:
+    arr = _segments(segs)
+    return load().dfr_sort_batch(arr, len(segs), _ptr(ws), int(ws_bytes), _stream(stream))
+
+
+def dfr_set_debug(spin_limit: int = 0, force_timeout: bool = False) -> int:
+    return load().dfr_set_debug(int(spin_limit), 1 if force_timeout else 0)
+
+
+def dfr_profile_enable(on: bool) -> int:
+    return load().dfr_profile_enable(1 if on else 0)
+
+
+def dfr_profile_read() -> dict:
+    ms = (ctypes.c_double * DFR_PROFILE_KINDS)()
+    n = (_u64 * DFR_PROFILE_KINDS)()
+    check(load().dfr_profile_read(ms, n), "dfr_profile_read")
+    lib = load()
+    return {lib.dfr_profile_kind_name(i).decode(): (float(ms[i]), int(n[i])) for i in range(DFR_PROFILE_KINDS)}
+
+
+def dfr_launch_count() -> int:
+    return int(load().dfr_launch_count())
+
+
+def dfr_status_string(code: int) -> str:
+    return load().dfr_status_string(int(code)).decode()
+
+
+# ------------------------------------------------------ torch conveniences
+
+class Sorter:
+    """Holds a scratch buffer and a workspace (allocated with torch) sized for
+    up to `capacity` keys of `key_type`, and sorts device tensors in place
+    through the C entry points above."""
+
+    def __init__(self, key_type: int, capacity: int, device="cuda"):
+        import torch
+
+        self.key_type = key_type
+        self.capacity = int(capacity)
+        self.device = torch.device(device)
+        kb = KEY_BYTES[key_type]
+        kdt = torch.int32 if kb == 4 else torch.int64
+        self.kbuf = torch.empty(max(1, self.capacity), dtype=kdt, device=self.device)
+        self.vbuf = (torch.empty(max(1, self.capacity), dtype=torch.int32, device=self.device)
+                     if HAS_VALS[key_type] else None)
+        self.ws_bytes = dfr_workspace_bytes(key_type, max(2, self.capacity))
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+
+    def sort_(self, keys, vals=None, n=None, stream=None) -> int:
+        n = int(keys.numel() if n is None else n)
+        if n > self.capacity:
+            raise ValueError("array of %d keys exceeds capacity %d" % (n, self.capacity))
+        kt = self.key_type
+        if kt == DFR_U32:
+            rc = dfr_sort_u32(keys, self.kbuf, n, self.ws, self.ws_bytes, stream)
+        elif kt == DFR_U64:
+            rc = dfr_sort_u64(keys, self.kbuf, n, self.ws, self.ws_bytes, stream)
+        elif kt == DFR_U64_KV:
+            rc = dfr_sort_u64_kv(keys, vals, self.kbuf, self.vbuf, n, self.ws, self.ws_bytes, stream)
+        else:
+            rc = dfr_sort_u32_kv(keys, vals, self.kbuf, self.vbuf, n, self.ws, self.ws_bytes, stream)
+        check(rc, "sort")
+        return rc
+
+    def device_status(self, stream=None) -> int:
+        return dfr_last_device_status(self.ws, stream)
+
+    def stats(self, stream=None) -> dict:
+        return dfr_get_stats(self.ws, stream)
+
+
+def to_device(a, device="cuda"):
+    """numpy uint32/uint64 array -> torch int32/int64 device tensor holding the
+    same bits (torch's unsigned dtypes have patchy op coverage)."""
+    import numpy as np
+    import torch
+
+    if a.dtype == np.uint32:
+        t = torch.from_numpy(np.ascontiguousarray(a).view(np.int32))
+    elif a.dtype == np.uint64:
+        t = torch.from_numpy(np.ascontiguousarray(a).view(np.int64))
+    else:
+        t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.to(device)
+
+
+def to_numpy(t, dtype):
+    """Device tensor -> numpy array reinterpreted as `dtype` (np.uint32/uint64)."""
+    import numpy as np
+
+    return t.cpu().numpy().view(dtype)

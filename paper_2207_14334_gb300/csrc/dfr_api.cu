@@ -1,0 +1,278 @@
+// dfr_api.cu -- the C ABI declared in include/dfr.h: argument marshalling to
+// the per-type drivers, device status and statistics readback, debug knobs
+// and launch profiling.
+#include <atomic>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "dfr_host.cuh"
+
+namespace dfr {
+
+namespace {
+
+constexpr uint32_t kDefaultSpinLimit = 1u << 18;
+
+std::atomic<uint32_t> g_spin_limit{kDefaultSpinLimit};
+std::atomic<int> g_force_timeout{0};
+std::atomic<int> g_profile{0};
+std::atomic<uint64_t> g_launches{0};
+
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+std::vector<ProfRec> g_prof_recs;
+std::vector<cudaEvent_t> g_prof_pending;  // start event of the launch in flight
+
+std::mutex g_grid_mu;
+std::map<std::pair<const void*, int>, int> g_grid_cache;
+
+}  // namespace
+
+uint32_t rt_spin_limit() { return g_spin_limit.load(); }
+int rt_force_timeout() { return g_force_timeout.load(); }
+void rt_count_launch() { g_launches.fetch_add(1); }
+
+void rt_prof_begin(int, cudaStream_t st) {
+  if (!g_profile.load()) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, st);
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  g_prof_pending.push_back(e);
+}
+
+void rt_prof_end(int kind, cudaStream_t st) {
+  if (!g_profile.load()) return;
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  if (g_prof_pending.empty()) return;
+  cudaEvent_t a = g_prof_pending.back();
+  g_prof_pending.pop_back();
+  cudaEvent_t b;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return;
+  }
+  cudaEventRecord(b, st);
+  g_prof_recs.push_back(ProfRec{kind, a, b});
+}
+
+int rt_grid(const void* kern, int threads, size_t smem) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(g_grid_mu);
+  auto key = std::make_pair(kern, dev);
+  auto it = g_grid_cache.find(key);
+  if (it != g_grid_cache.end()) return it->second;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  if (sms < 1) sms = 1;
+  const int grid = sms * per_sm;
+  g_grid_cache[key] = grid;
+  return grid;
+}
+
+static int map_device_status(uint32_t err) {
+  if (err & DERR_TIMEOUT) return DFR_ERR_TIMEOUT;
+  if (err & DERR_BOUNDS) return DFR_ERR_BOUNDS;
+  if (err & DERR_CAPACITY) return DFR_ERR_WORKSPACE;
+  return DFR_OK;
+}
+
+static int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb,
+                     cudaStream_t st) {
+  switch (key_type) {
+    case DFR_U32: return run_u32(a, n, batch, ws, wsb, st);
+    case DFR_U32_KV: return run_u32_kv(a, n, batch, ws, wsb, st);
+    case DFR_U64: return run_u64(a, n, batch, ws, wsb, st);
+    case DFR_U64_KV: return run_u64_kv(a, n, batch, ws, wsb, st);
+    default: return DFR_ERR_INVALID_ARG;
+  }
+}
+
+static int ws_typed(int key_type, uint64_t ntot, uint32_t narr, size_t* bytes) {
+  switch (key_type) {
+    case DFR_U32: *bytes = ws_u32(ntot, narr); return DFR_OK;
+    case DFR_U32_KV: *bytes = ws_u32_kv(ntot, narr); return DFR_OK;
+    case DFR_U64: *bytes = ws_u64(ntot, narr); return DFR_OK;
+    case DFR_U64_KV: *bytes = ws_u64_kv(ntot, narr); return DFR_OK;
+    default: return DFR_ERR_INVALID_ARG;
+  }
+}
+
+}  // namespace dfr
+
+using namespace dfr;
+
+extern "C" {
+
+int dfr_workspace_bytes(int key_type, uint64_t n, size_t* bytes) {
+  if (!bytes || n > DFR_MAX_N) return DFR_ERR_INVALID_ARG;
+  return ws_typed(key_type, n, 1u, bytes);
+}
+
+int dfr_sort_u32(uint32_t* keys, uint32_t* buf, uint64_t n, void* ws, size_t ws_bytes, dfr_stream_t stream) {
+  const HostArr a{keys, buf, nullptr, nullptr, n};
+  return run_u32(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int dfr_sort_u64(uint64_t* keys, uint64_t* buf, uint64_t n, void* ws, size_t ws_bytes, dfr_stream_t stream) {
+  const HostArr a{keys, buf, nullptr, nullptr, n};
+  return run_u64(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int dfr_sort_u64_kv(uint64_t* keys, uint32_t* vals, uint64_t* kbuf, uint32_t* vbuf, uint64_t n, void* ws,
+                    size_t ws_bytes, dfr_stream_t stream) {
+  const HostArr a{keys, kbuf, vals, vbuf, n};
+  return run_u64_kv(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int dfr_sort_u32_kv(uint32_t* keys, uint32_t* vals, uint32_t* kbuf, uint32_t* vbuf, uint64_t n, void* ws,
+                    size_t ws_bytes, dfr_stream_t stream) {
+  const HostArr a{keys, kbuf, vals, vbuf, n};
+  return run_u32_kv(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int dfr_last_device_status(const void* ws, dfr_stream_t stream, int* status) {
+  if (!ws || !status) return DFR_ERR_INVALID_ARG;
+  uint32_t err = 0;
+  if (cudaMemcpyAsync(&err, ws, sizeof(err), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
+    return DFR_ERR_CUDA;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return DFR_ERR_CUDA;
+  *status = map_device_status(err);
+  return DFR_OK;
+}
+
+int dfr_get_stats(const void* ws, dfr_stream_t stream, dfr_stats_t* out) {
+  if (!ws || !out) return DFR_ERR_INVALID_ARG;
+  Ctl h;
+  if (cudaMemcpyAsync(&h, ws, sizeof(Ctl), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
+    return DFR_ERR_CUDA;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return DFR_ERR_CUDA;
+  std::memset(out, 0, sizeof(*out));
+  out->n_total = h.n_total;
+  out->key_bytes = h.key_bytes;
+  out->val_bytes = h.val_bytes;
+  out->device_status = (uint32_t)map_device_status(h.err);
+  uint32_t levels = 0;
+  for (int L = 0; L < MAXLV && L < DFR_STATS_MAX_LEVELS; ++L) {
+    out->level_segments[L] = h.lv[L].nseg;
+    out->level_tiles[L] = h.lv[L].ntiles;
+    out->level_keys[L] = h.lv[L].keys;
+    out->level_hist_keys[L] = h.lv[L].hist_keys;
+    if (h.lv[L].nseg) levels = (uint32_t)L + 1;
+  }
+  out->levels = levels;
+  out->cta_buckets = h.cta_buckets;
+  out->cta_keys = h.cta_keys;
+  out->tiny_buckets = h.tiny_buckets;
+  out->tiny_keys = h.tiny_keys;
+  out->const_buckets = h.const_buckets;
+  out->const_keys = h.const_keys;
+  out->copy_keys = h.copy_keys;
+  // Minimal bytes of the executed plan: one read of every key (root count);
+  // a read and a write of every record per partition level it is dealt in;
+  // a read and a write of every record sorted by a diversion sort; a read and
+  // a write of every constant record that has to move back from the buffer.
+  // Re-reads by per-level counts are not charged (they could be fused).
+  const uint64_t rec = (uint64_t)h.key_bytes + h.val_bytes;
+  uint64_t b = h.n_total * h.key_bytes;
+  for (int L = 0; L < MAXLV; ++L) b += 2 * rec * h.lv[L].keys;
+  b += 2 * rec * (h.cta_keys + h.tiny_keys + h.copy_keys);
+  out->model_bytes = b;
+  return DFR_OK;
+}
+
+int dfr_batch_workspace_bytes(const dfr_segment_t* segs, uint32_t count, size_t* bytes) {
+  if (!bytes || (!segs && count)) return DFR_ERR_INVALID_ARG;
+  if (count == 0) {
+    *bytes = 0;
+    return DFR_OK;
+  }
+  const int kt = segs[0].key_type;
+  uint64_t ntot = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    if (segs[i].key_type != kt || segs[i].n > DFR_MAX_N) return DFR_ERR_INVALID_ARG;
+    ntot += segs[i].n;
+  }
+  return ws_typed(kt, ntot, count, bytes);
+}
+
+int dfr_sort_batch(const dfr_segment_t* segs, uint32_t count, void* ws, size_t ws_bytes, dfr_stream_t stream) {
+  if (count == 0) return DFR_OK;
+  if (!segs) return DFR_ERR_INVALID_ARG;
+  const int kt = segs[0].key_type;
+  std::vector<HostArr> a(count);
+  for (uint32_t i = 0; i < count; ++i) {
+    if (segs[i].key_type != kt) return DFR_ERR_INVALID_ARG;
+    a[i] = HostArr{segs[i].keys, segs[i].kbuf, segs[i].vals, segs[i].vbuf, segs[i].n};
+  }
+  return run_typed(kt, a.data(), count, true, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int dfr_set_debug(uint32_t spin_limit, int force_timeout) {
+  g_spin_limit.store(spin_limit ? spin_limit : kDefaultSpinLimit);
+  g_force_timeout.store(force_timeout ? 1 : 0);
+  return DFR_OK;
+}
+
+int dfr_profile_enable(int on) {
+  g_profile.store(on ? 1 : 0);
+  return DFR_OK;
+}
+
+int dfr_profile_read(double* ms_total, uint64_t* launches) {
+  if (!ms_total || !launches) return DFR_ERR_INVALID_ARG;
+  for (int i = 0; i < DFR_PROFILE_KINDS; ++i) {
+    ms_total[i] = 0.0;
+    launches[i] = 0;
+  }
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  int rc = DFR_OK;
+  for (auto& r : g_prof_recs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+      rc = DFR_ERR_CUDA;
+    if (r.kind >= 0 && r.kind < DFR_PROFILE_KINDS) {
+      ms_total[r.kind] += ms;
+      launches[r.kind] += 1;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_prof_recs.clear();
+  return rc;
+}
+
+const char* dfr_profile_kind_name(int kind) {
+  static const char* names[DFR_PROFILE_KINDS] = {"init",     "root_count", "root_classify", "level_count",
+                                                  "scatter",  "classify",   "ctasort",       "copy",
+                                                  "h2d",      "other"};
+  return (kind >= 0 && kind < DFR_PROFILE_KINDS) ? names[kind] : "unknown";
+}
+
+uint64_t dfr_launch_count(void) { return g_launches.load(); }
+
+const char* dfr_status_string(int status) {
+  switch (status) {
+    case DFR_OK: return "ok";
+    case DFR_ERR_INVALID_ARG: return "invalid argument";
+    case DFR_ERR_WORKSPACE: return "workspace too small or device queue overflow";
+    case DFR_ERR_CUDA: return "CUDA runtime error";
+    case DFR_ERR_TIMEOUT: return "device-side wait timed out";
+    case DFR_ERR_OVER_BUDGET: return "request exceeds the memory budget";
+    case DFR_ERR_BUSY: return "busy";
+    case DFR_ERR_BOUNDS: return "device-side bounds check failed";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

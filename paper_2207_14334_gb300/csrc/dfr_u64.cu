@@ -1,0 +1,12 @@
+// dfr_u64.cu -- instantiation of the DFR sort driver for key type uint64_t, payload NoVal.
+#include "dfr_host.cuh"
+
+namespace dfr {
+
+int run_u64(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st) {
+  return run_sort<uint64_t, NoVal>(a, n, batch, ws, wsb, st);
+}
+
+size_t ws_u64(uint64_t ntot, uint32_t narr) { return workspace_bytes<uint64_t, NoVal>(ntot, narr); }
+
+}  // namespace dfr

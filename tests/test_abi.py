@@ -1,0 +1,91 @@
+"""The C-ABI library loads, exports every symbol include/dfr.h declares, and its
+host-side argument checks behave as documented (no GPU needed: every call
+here returns before touching CUDA)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2207_14334_gb300 as dfr
+from paper_2207_14334_gb300 import build as dfr_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dfr.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    dfr_build.build()
+    return dfr.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(dfr_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("dfr_sort_u32", "dfr_sort_u64", "dfr_sort_u64_kv", "dfr_sort_batch",
+                     "dfr_workspace_bytes", "dfr_last_device_status", "dfr_get_stats"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_workspace_bytes(lib):
+    small = dfr.dfr_workspace_bytes(dfr.DFR_U32, 1000)
+    big = dfr.dfr_workspace_bytes(dfr.DFR_U32, 1 << 28)
+    assert 0 < small < big
+    # the workspace stays a modest fraction of the key array at full size
+    assert big < 0.5 * (1 << 28) * 4
+    for kt in (dfr.DFR_U64, dfr.DFR_U64_KV, dfr.DFR_U32_KV):
+        assert dfr.dfr_workspace_bytes(kt, 1 << 20) > 0
+    out = ctypes.c_size_t(0)
+    assert lib.dfr_workspace_bytes(99, 10, ctypes.byref(out)) == dfr.DFR_ERR_INVALID_ARG
+    assert lib.dfr_workspace_bytes(dfr.DFR_U32, dfr.DFR_MAX_N + 1, ctypes.byref(out)) == dfr.DFR_ERR_INVALID_ARG
+    assert lib.dfr_workspace_bytes(dfr.DFR_U32, 10, None) == dfr.DFR_ERR_INVALID_ARG
+
+
+def test_host_argument_checks(lib):
+    # n == 0 and n == 1 are no-ops
+    assert dfr.dfr_sort_u32(0, 0, 0, 0, 0, stream=0) == dfr.DFR_OK
+    assert dfr.dfr_sort_u32(0x1000, 0x2000, 1, 0, 0, stream=0) == dfr.DFR_OK
+    # null pointers
+    assert dfr.dfr_sort_u32(0, 0x2000, 10, 0x10000, 1 << 20, stream=0) == dfr.DFR_ERR_INVALID_ARG
+    assert dfr.dfr_sort_u64_kv(0x1000, 0, 0x9000, 0xA000, 10, 0x10000, 1 << 20, stream=0) == dfr.DFR_ERR_INVALID_ARG
+    # overlapping keys / buf
+    assert dfr.dfr_sort_u32(0x1000, 0x1010, 100, 0x100000, 1 << 24, stream=0) == dfr.DFR_ERR_INVALID_ARG
+    assert dfr.dfr_sort_u64_kv(0x1000, 0x1100, 0x100000, 0x200000, 100, 0x1000000, 1 << 24,
+                               stream=0) == dfr.DFR_ERR_INVALID_ARG
+    # n above the maximum
+    assert dfr.dfr_sort_u32(0x1000, 0x10000000000, dfr.DFR_MAX_N + 1, 0x100000, 1 << 24,
+                            stream=0) == dfr.DFR_ERR_INVALID_ARG
+    # misaligned or missing workspace
+    ws = dfr.dfr_workspace_bytes(dfr.DFR_U32, 1000)
+    assert dfr.dfr_sort_u32(0x100000, 0x200000, 1000, 0x300010, ws, stream=0) == dfr.DFR_ERR_INVALID_ARG
+    assert dfr.dfr_sort_u32(0x100000, 0x200000, 1000, 0, ws, stream=0) == dfr.DFR_ERR_INVALID_ARG
+    # workspace too small
+    assert dfr.dfr_sort_u32(0x100000, 0x200000, 1000, 0x300000, ws - 1, stream=0) == dfr.DFR_ERR_WORKSPACE
+
+
+def test_batch_host_checks(lib):
+    segs = [(dfr.DFR_U32, 0x100000, 0, 0x200000, 0, 1000), (dfr.DFR_U64, 0x300000, 0, 0x400000, 0, 10)]
+    with pytest.raises(dfr.DfrError):
+        dfr.dfr_batch_workspace_bytes(segs)
+    assert dfr.dfr_sort_batch(segs, 0x1000000, 1 << 30, stream=0) == dfr.DFR_ERR_INVALID_ARG
+    one = [(dfr.DFR_U32, 0x100000, 0, 0x200000, 0, 1000)]
+    assert dfr.dfr_batch_workspace_bytes(one) >= dfr.dfr_workspace_bytes(dfr.DFR_U32, 1000)
+    assert dfr.dfr_sort_batch([], 0, 0, stream=0) == dfr.DFR_OK
+
+
+def test_status_strings_and_counters(lib):
+    for code in range(8):
+        assert dfr.dfr_status_string(code)
+    assert dfr.dfr_launch_count() >= 0
+    assert dfr.dfr_set_debug(0, False) == dfr.DFR_OK
