@@ -51,9 +51,11 @@ WORKLOADS = {
     "plain_u32_2^28": dict(kind="plain", key="u32", n=1 << 28, dists=list(synth.U32_DISTRIBUTIONS)),
     "plain_u32_1M": dict(kind="plain", key="u32", n=1_000_000, dists=["uniform"]),
     "kv_u64_2^27": dict(kind="plain", key="u64kv", n=1 << 27, dists=list(synth.U64_DISTRIBUTIONS)),
+    # a smaller case (still larger than L2) for full ncu captures
+    "plain_u32_2^26": dict(kind="plain", key="u32", n=1 << 26, dists=["uniform"]),
 }
 DEFAULT_WORKLOAD = "plain_u32_2^28"
-SEED_OFFSET = {"plain_u32_2^28": 20, "plain_u32_1M": 1, "kv_u64_2^27": 30}
+SEED_OFFSET = {"plain_u32_2^28": 20, "plain_u32_1M": 1, "kv_u64_2^27": 30, "plain_u32_2^26": 20}
 
 
 def kernel_source_sha() -> str:
@@ -233,8 +235,11 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample", type=int, default=1 << 24)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dists", default="", help="comma-separated subset of the workload's distributions")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.dists:
+        wl["dists"] = [d for d in args.dists.split(",") if d in wl["dists"]]
     rank, world, local = dist_setup()
 
     if args.impl == "reference":
