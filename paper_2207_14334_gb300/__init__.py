@@ -249,7 +249,8 @@ class Sorter:
         self.vbuf = (torch.empty(max(1, self.capacity), dtype=torch.int32, device=self.device)
                      if HAS_VALS[key_type] else None)
         self.ws_bytes = dfr_workspace_bytes(key_type, max(2, self.capacity))
-        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        # zeroed once so the status word reads DFR_OK before the first call
+        self.ws = torch.zeros(self.ws_bytes, dtype=torch.uint8, device=self.device)
 
     def sort_(self, keys, vals=None, n=None, stream=None) -> int:
         n = int(keys.numel() if n is None else n)

@@ -41,8 +41,9 @@ def gpu_sort(dfr, keys, vals=None, key_type=None):
     s = sorter(dfr, key_type, n)
     dk = dfr.to_device(keys) if n else None
     dv = dfr.to_device(vals) if (vals is not None and n) else None
-    if n == 0:
-        return keys.copy(), (None if vals is None else vals.copy()), dfr.DFR_OK
+    if n <= 1:  # nothing is launched for n <= 1
+        rc = s.sort_(dk, dv, n) if n else dfr.DFR_OK
+        return keys.copy(), (None if vals is None else vals.copy()), rc
     s.sort_(dk, dv)
     status = s.device_status()
     k = dfr.to_numpy(dk, keys.dtype)
