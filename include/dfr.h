@@ -54,7 +54,8 @@ enum dfr_status {
     DFR_ERR_TIMEOUT = 4,      /* a device-side wait gave up after its iteration limit */
     DFR_ERR_OVER_BUDGET = 5,  /* a served request exceeds the server's memory budget */
     DFR_ERR_BUSY = 6,         /* the server cannot take the request now */
-    DFR_ERR_BOUNDS = 7        /* a device-side bounds check rejected a write (result invalid) */
+    DFR_ERR_BOUNDS = 7,       /* a device-side bounds check rejected a write (result invalid) */
+    DFR_ERR_TOO_LARGE = 8     /* more keys than dfr_sort_u32_noalloc's fixed scratch holds */
 };
 
 enum dfr_key_type {
@@ -132,6 +133,33 @@ typedef struct {
 /* dfr_get_stats -- wait for `stream` and copy the counters of the last call
  * that used `ws` into *out.  DFR_ERR_CUDA on a failed copy. */
 int dfr_get_stats(const void* ws, dfr_stream_t stream, dfr_stats_t* out);
+
+/*
+ * dfr_sort_u32_noalloc -- dfr_sort_u32 for callers that cannot allocate
+ * device memory.  The paper has no counterpart: it is a deployment variant.
+ *
+ * Some callers cannot hand over a scratch buffer and a workspace: a plug-in
+ * inside a host application that owns all device memory through its own
+ * allocator, code running under a strict per-process memory quota, or a
+ * latency-critical loop that must not pay cudaMalloc's implicit device
+ * synchronisation.  This call needs only the keys: its scratch buffer and
+ * workspace live in a fixed device array inside the library, which every GPU
+ * that loads the library holds until the process exits.
+ *   keys  [n] device, in/out;  n <= DFR_NOALLOC_MAX_N.
+ * Returns DFR_ERR_TOO_LARGE for n > DFR_NOALLOC_MAX_N (nothing enqueued),
+ * DFR_ERR_INVALID_ARG for a null or misaligned `keys`, DFR_ERR_CUDA if the
+ * launch or the one-time set-up fails.  It calls no cudaMalloc, no cudaFree
+ * and no allocating library routine.
+ * The first call on a device (with that device current) resolves the fixed
+ * array's device address; make that first call before any stream capture.
+ * Every call on a device shares the one array, which keeps the previous
+ * call's contents; the call clears what must start at zero itself.  Calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on
+ * the array: serialise them.  Device-side errors of this call are not
+ * reported (there is no caller-visible workspace to hold the status word).
+ */
+#define DFR_NOALLOC_MAX_N ((uint64_t)1u << 20)
+int dfr_sort_u32_noalloc(uint32_t* keys, uint64_t n, dfr_stream_t stream);
 
 /* ---------------------------------------------------------------- batch -- */
 

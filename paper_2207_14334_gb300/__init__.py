@@ -26,6 +26,7 @@ DFR_ERR_TIMEOUT = 4
 DFR_ERR_OVER_BUDGET = 5
 DFR_ERR_BUSY = 6
 DFR_ERR_BOUNDS = 7
+DFR_ERR_TOO_LARGE = 8
 
 DFR_U32 = 0
 DFR_U64 = 1
@@ -33,6 +34,7 @@ DFR_U64_KV = 2
 DFR_U32_KV = 3
 
 DFR_MAX_N = (1 << 30) - 1
+DFR_NOALLOC_MAX_N = 1 << 20
 DFR_PROFILE_KINDS = 10
 DFR_STATS_MAX_LEVELS = 16
 
@@ -72,6 +74,7 @@ _SIGNATURES = {
     "dfr_sort_u64": (ctypes.c_int, [_vp, _vp, _u64, _vp, _sz, _vp]),
     "dfr_sort_u64_kv": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp]),
     "dfr_sort_u32_kv": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp]),
+    "dfr_sort_u32_noalloc": (ctypes.c_int, [_vp, _u64, _vp]),
     "dfr_last_device_status": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_int)]),
     "dfr_get_stats": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(dfr_stats_t)]),
     "dfr_batch_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(dfr_segment_t), _u32, ctypes.POINTER(_sz)]),
@@ -164,6 +167,12 @@ def dfr_sort_u64_kv(keys, vals, kbuf, vbuf, n, ws, ws_bytes, stream=None) -> int
 def dfr_sort_u32_kv(keys, vals, kbuf, vbuf, n, ws, ws_bytes, stream=None) -> int:
     return load().dfr_sort_u32_kv(_ptr(keys), _ptr(vals), _ptr(kbuf), _ptr(vbuf), int(n), _ptr(ws),
                                   int(ws_bytes), _stream(stream))
+
+
+def dfr_sort_u32_noalloc(keys, n, stream=None) -> int:
+    """u32 sort whose scratch lives in the library's fixed device array
+    (for callers that cannot allocate device memory; n <= DFR_NOALLOC_MAX_N)."""
+    return load().dfr_sort_u32_noalloc(_ptr(keys), int(n), _stream(stream))
 
 
 def dfr_last_device_status(ws, stream=None) -> int:

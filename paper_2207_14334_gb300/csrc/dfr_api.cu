@@ -271,6 +271,7 @@ const char* dfr_status_string(int status) {
     case DFR_ERR_OVER_BUDGET: return "request exceeds the memory budget";
     case DFR_ERR_BUSY: return "busy";
     case DFR_ERR_BOUNDS: return "device-side bounds check failed";
+    case DFR_ERR_TOO_LARGE: return "more keys than the fixed no-allocation scratch holds";
     default: return "unknown status";
   }
 }
