@@ -334,12 +334,18 @@ def main():
     dfr.dfr_profile_enable(True)
     dfr.dfr_profile_read()
     plan = {}
+    prof_by_dist = {}
+    prof = {}
     for d in inputs:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         one_sort(d, e0, e1)
         torch.cuda.synchronize()
         plan[d] = sorter.stats(stream)
-    prof = dfr.dfr_profile_read()
+        pd = dfr.dfr_profile_read()
+        prof_by_dist[d] = {k: round(v[0], 4) for k, v in pd.items() if v[1]}
+        for k, (ms_k, n_k) in pd.items():
+            a, b = prof.get(k, (0.0, 0))
+            prof[k] = (a + ms_k, b + n_k)
     dfr.dfr_profile_enable(False)
     rec = wbytes + vbytes
     scatter_keys = sum(sum(p["level_keys"]) for p in plan.values())
@@ -360,7 +366,8 @@ def main():
         per_dist[d] = {"ms": t, "gkeys_s": n / (t * 1e-3) / 1e9, "model_bytes": p["model_bytes"],
                        "sort_roofline_frac": p["model_bytes"] / (t * 1e-3) / 1e9 / peak,
                        "levels": p["levels"], "level_keys": [k for k in p["level_keys"] if k],
-                       "cta_keys": p["cta_keys"], "tiny_keys": p["tiny_keys"], "const_keys": p["const_keys"]}
+                       "cta_keys": p["cta_keys"], "wsort_keys": p["wsort_keys"], "tiny_keys": p["tiny_keys"],
+                       "const_keys": p["const_keys"], "kernel_ms": prof_by_dist[d]}
     kernel_share = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}
 
     # End to end through the C ABI: pinned host keys -> device -> sort -> host.

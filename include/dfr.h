@@ -128,6 +128,9 @@ typedef struct {
     uint64_t const_buckets, const_keys;                /* constant buckets left alone */
     uint64_t copy_keys;                                /* constant keys moved back from buf */
     uint64_t model_bytes;                              /* minimal bytes of the executed plan */
+    uint64_t wsort_buckets, wsort_keys;                /* diverted to the warp shared-memory sort */
+    uint32_t device_error_site;                        /* first failed device check (0 = none; see dfr_api.cu) */
+    uint32_t reserved;
 } dfr_stats_t;
 
 /* dfr_get_stats -- wait for `stream` and copy the counters of the last call

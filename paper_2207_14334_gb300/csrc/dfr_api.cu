@@ -186,8 +186,12 @@ int dfr_get_stats(const void* ws, dfr_stream_t stream, dfr_stats_t* out) {
   const uint64_t rec = (uint64_t)h.key_bytes + h.val_bytes;
   uint64_t b = h.n_total * h.key_bytes;
   for (int L = 0; L < MAXLV; ++L) b += 2 * rec * h.lv[L].keys;
-  b += 2 * rec * (h.cta_keys + h.tiny_keys + h.copy_keys);
+  b += 2 * rec * (h.cta_keys + h.wsort_keys + h.tiny_keys + h.copy_keys);
   out->model_bytes = b;
+  out->wsort_buckets = h.wsort_buckets;
+  // 1 scatter staging, 2 scatter write, 3 CTA-sort staging, 4 warp-sort staging, 5 look-back timeout
+  out->device_error_site = h.err_site;
+  out->wsort_keys = h.wsort_keys;
   return DFR_OK;
 }
 
@@ -255,7 +259,7 @@ int dfr_profile_read(double* ms_total, uint64_t* launches) {
 const char* dfr_profile_kind_name(int kind) {
   static const char* names[DFR_PROFILE_KINDS] = {"init",     "root_count", "root_classify", "level_count",
                                                   "scatter",  "classify",   "ctasort",       "copy",
-                                                  "h2d",      "other"};
+                                                  "h2d",      "warpsort"};
   return (kind >= 0 && kind < DFR_PROFILE_KINDS) ? names[kind] : "unknown";
 }
 

@@ -12,27 +12,32 @@
 //   * Every array is a root segment.  k_root_count reads each key once and
 //     produces, per array, the AND and OR of its keys and the histogram of its
 //     top byte.  k_root_classify drops constant arrays, diverts small ones and
-//     turns the rest into level-0 segments whose digit window sits at the
-//     array's highest varying bit (pass skipping, Section LSD).
-//   * One level = k_level_count (histogram of the segment's digit, skipped
-//     when the root count already has it) + k_scatter (single-pass decoupled
-//     look-back over tiles, shared-memory staging so every run of a digit is
-//     written contiguously; it also folds the AND/OR of every destination
-//     bucket) + k_classify (per bucket: empty, constant, tiny, CTA-sized or
-//     large; large buckets become the next level's segments with their window
-//     again at the bucket's highest varying bit).
+//     turns the rest into level-0 segments whose 8-bit digit window sits at
+//     the array's highest varying bit (pass skipping, Section LSD).
+//   * One level = k_level_count (histogram of each segment's window and the
+//     AND/OR of its keys) + k_scatter (single-pass decoupled look-back over
+//     tiles, shared-memory staging so every run of a digit is written
+//     contiguously) + k_classify (per segment: constant -> finished; window
+//     without varying bits -> re-windowed at the highest varying bit without
+//     moving data; else per bucket: empty, tiny, CTA-sized or large -> next
+//     level).  Every level lowers the window top by at least 8 bits, so a
+//     W-bit key needs at most W/8 levels.
 //   * Diverted buckets: tiny ones (<= T_WARP keys) are sorted by one warp
 //     inside k_classify; mid-size ones (<= T_CTA) are queued and sorted by
-//     k_ctasort, a stable LSD radix sort in shared memory over the bucket's
-//     varying bits only.  Constant buckets that ended in the buffer are
-//     copied back (small ones by the same queues, large ones by k_copy).
+//     k_ctasort, an LSD radix sort in shared memory over the bucket's varying
+//     bits only.  Constant buckets that ended in the buffer are copied back
+//     (small ones through the same queues, large ones by k_copy).
 //   * All kernels are persistent: they pull tiles/segments/items from device
 //     counters, so the host never waits on the device between kernels and the
 //     number of launches is independent of the data and of the array count.
 //
-// Stability: the in-tile ranking is in element order, tiles are combined in
-// tile order by the look-back, and both diversion sorts are stable, so the
-// result is the stable sort by key (payloads keep input order on ties).
+// Ranking inside a tile: key-only sorts rank with warp-private shared-memory
+// counters (count, then cursor) in whatever order the atomics resolve -- the
+// order of equal digits inside a bucket cannot change the output, because
+// every bucket is later sorted by its remaining bits and equal keys are
+// indistinguishable.  Key-value sorts rank stably (element order, full-warp
+// ballot peer matching), tiles are chained in tile order by the look-back and
+// the diversion sorts are stable, so payloads keep input order on ties.
 #pragma once
 
 #include <cstdint>
@@ -48,12 +53,17 @@ constexpr int M = 1 << RB;    // buckets per partition pass
 constexpr uint32_t FLAG_AGG = 1u << 30;    // look-back: tile aggregate only
 constexpr uint32_t FLAG_INC = 2u << 30;    // look-back: inclusive prefix
 constexpr uint32_t COUNT_MASK = (1u << 30) - 1u;
-constexpr int MAXLV = 9;      // levels of control blocks (>= key bits / RB + 1)
+constexpr int MAXLV = 12;     // control blocks per level (>= launched levels + 1)
+constexpr int EXTRA_LEVELS = 2;  // levels launched beyond key bits / RB (room for narrow windows)
 constexpr uint32_t T_WARP = 32;  // tiny-bucket threshold (warp sort)
 
 enum : uint32_t { DERR_TIMEOUT = 1u, DERR_BOUNDS = 2u, DERR_CAPACITY = 4u };
+enum : uint32_t {
+  ERR_SITE_SCATTER_STAGE = 1u, ERR_SITE_SCATTER_WRITE, ERR_SITE_CTASORT_STAGE, ERR_SITE_WARPSORT_STAGE,
+  ERR_SITE_LOOKBACK
+};
 constexpr uint32_t NO_OWNER = 0xffffffffu;  // tile-owner entry of a tile that must be skipped
-enum : uint32_t { SEG_NEEDS_HIST = 1u };
+enum : uint32_t { SEG_NEEDS_HIST = 1u, SEG_NEEDS_ANDOR = 2u };
 enum : uint32_t { ITEM_PARITY = 1u, ITEM_COPY = 2u };
 
 struct NoVal {};
@@ -76,8 +86,10 @@ struct Seg {
   uint32_t tile_start;  // first global tile of this segment at its level
   uint32_t shift;       // digit = (key >> shift) & (M-1)
   uint32_t parity;      // 0: data in keys, 1: data in buf
-  uint32_t flags;       // SEG_NEEDS_HIST
-  uint32_t pad;
+  uint32_t flags;       // SEG_NEEDS_HIST | SEG_NEEDS_ANDOR
+  uint32_t bits;        // varying bits the window covers (window = [shift, shift + bits))
+  unsigned long long nand;  // OR of ~key over the segment (AND = ~nand)
+  unsigned long long orv;   // OR of key over the segment
 };
 
 // A mid-size bucket for k_ctasort (or a mid-size constant bucket to copy back).
@@ -103,12 +115,14 @@ struct LevelCtl {
   uint32_t hist_claim;
   uint32_t scat_claim;
   unsigned long long keys;       // keys dealt at this level
-  unsigned long long hist_keys;  // keys re-read by k_level_count
+  unsigned long long hist_keys;  // keys read by k_level_count
 };
 
 struct Ctl {
   uint32_t err;
-  uint32_t never;  // a status word nobody sets (forced-timeout test mode)
+  uint32_t never;     // a status word nobody sets (forced-timeout test mode)
+  uint32_t err_site;  // first place a device check failed (ERR_SITE_*), 0 if none
+  uint32_t pad0;
   uint32_t root_claim;
   uint32_t cta_count;
   uint32_t cta_claim;
@@ -117,9 +131,11 @@ struct Ctl {
   uint32_t copy_claim;
   uint32_t key_bytes;
   uint32_t val_bytes;
-  uint32_t pad[2];
+  uint32_t wq_count;
+  uint32_t wq_claim;
   unsigned long long n_total;
   unsigned long long cta_buckets, cta_keys;
+  unsigned long long wsort_buckets, wsort_keys;
   unsigned long long tiny_buckets, tiny_keys;
   unsigned long long const_buckets, const_keys;
   unsigned long long copy_keys;
@@ -142,15 +158,15 @@ struct Ctx {
   void* root;  // RootAcc<K>[narr]
   Seg* segs[2];
   uint32_t* hist[2];  // [segcap][M] per level parity
-  void* a_nand;       // K[segcap][M]
-  void* a_or;         // K[segcap][M]
   uint32_t* tile_owner;
   uint32_t* status;   // [tilecap][M] look-back words
   Item* cta_q;
+  Item* w_q;          // buckets for the warp sort
   CopyItem* copy_q;
   uint32_t* copy_owner;
-  uint32_t segcap, tilecap, ctacap, copycap, copytilecap;
+  uint32_t segcap, tilecap, ctacap, wqcap, copycap, copytilecap;
   uint32_t force_timeout;
+  uint32_t nlev;      // partition levels launched
 };
 
 // ------------------------------------------------------------------ helpers
@@ -206,20 +222,13 @@ __device__ __forceinline__ K warp_or(K x) {
   return x;
 }
 
-template <class K>
-__device__ __forceinline__ K group_or(uint32_t mask, K x) {
-  if constexpr (sizeof(K) == 8) {
-    const uint32_t lo = __reduce_or_sync(mask, (uint32_t)x);
-    const uint32_t hi = __reduce_or_sync(mask, (uint32_t)(x >> 32));
-    return ((K)hi << 32) | (K)lo;
-  } else {
-    return __reduce_or_sync(mask, (uint32_t)x);
-  }
-}
+__device__ __forceinline__ void atomic_or_u64(unsigned long long* p, unsigned long long v) { atomicOr(p, v); }
 
-__device__ __forceinline__ void atomic_or_k(uint32_t* p, uint32_t v) { atomicOr(p, v); }
-__device__ __forceinline__ void atomic_or_k(unsigned long long* p, unsigned long long v) {
-  atomicOr(p, v);
+// Record a failed device-side check: the error bit and, if it is the first,
+// where it happened.
+__device__ __forceinline__ void record_error(Ctl* ctl, uint32_t bit, uint32_t site) {
+  atomicOr(&ctl->err, bit);
+  atomicCAS(&ctl->err_site, 0u, site);
 }
 
 // Exclusive scan of one value per thread for threads [0, 256); every thread
@@ -247,81 +256,137 @@ __device__ __forceinline__ uint32_t scan256(uint32_t v, uint32_t* sh, uint32_t* 
   return pre + x - mine;
 }
 
-// Warp-aggregated shared-memory histogram increment: lanes holding the same
-// digit elect one lane that adds the group's size.
-__device__ __forceinline__ void hist_add(uint32_t* h, uint32_t d, bool valid) {
-  const uint32_t active = __ballot_sync(FULL, valid);
-  if (valid) {
-    const uint32_t peers = __match_any_sync(active, d);
-    if (lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+// Exclusive scan of one value per thread over the whole block of NT threads;
+// every thread must call it (it synchronises twice).  `sh` holds NT/32 words.
+template <int NT>
+__device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t* sh) {
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= (uint32_t)o) x += y;
   }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  uint32_t pre = 0;
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) pre += (i < (int)w) ? sh[i] : 0u;
+  __syncthreads();
+  return pre + x - v;
 }
 
-// Stable in-warp ranking of KPT warp-striped items (element i*32+lane of the
-// warp's chunk, `wvalid` of them valid): rank[i] = number of earlier elements
-// of the warp with the same digit plus the warp's running count of that digit
-// (kept in `wh`, this warp's private M counters).
+// Turn per-warp digit counts cnt[w][d] (NW x M words) into the shared-memory
+// position of the first element of digit d from warp w: the exclusive scan of
+// the counts taken in (digit, warp) order.  Each of the NT threads scans
+// NW * M / NT consecutive entries of that order.
+template <int NT, int NW>
+__device__ __forceinline__ void scan_digit_warp(uint32_t* cnt, uint32_t* sh) {
+  constexpr int E = NW * M / NT;
+  static_assert(E >= 1 && NW % E == 0, "entries per thread must split the warps of a digit");
+  const uint32_t first = threadIdx.x * E;
+  const uint32_t d = first / NW, w0 = first % NW;
+  uint32_t x[E];
+  uint32_t tot = 0;
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const uint32_t c = cnt[(w0 + q) * M + d];
+    x[q] = tot;
+    tot += c;
+  }
+  const uint32_t base = block_scan<NT>(tot, sh);
+#pragma unroll
+  for (int q = 0; q < E; ++q) cnt[(w0 + q) * M + d] = base + x[q];
+}
+
+// Add 1 to wh[d] for every valid lane; with RET, return each lane's distinct
+// pre-increment value (no particular order among lanes of equal digit).  A
+// warp whose valid lanes all hold one digit issues a single atomic.  Every
+// lane of the warp must call it.
+template <bool RET>
+__device__ __forceinline__ uint32_t warp_inc(uint32_t* wh, uint32_t d, bool valid) {
+  const uint32_t vmask = __ballot_sync(FULL, valid);
+  if (vmask == 0u) return 0u;
+  const int src = __ffs((int)vmask) - 1;
+  const uint32_t d0 = __shfl_sync(FULL, d, src);
+  if (__all_sync(FULL, !valid || d == d0)) {
+    uint32_t base = 0;
+    if ((int)lane_id() == src) base = atomicAdd(&wh[d0], (uint32_t)__popc(vmask));
+    if constexpr (RET) {
+      base = __shfl_sync(FULL, base, src);
+      return base + (uint32_t)__popc(vmask & lanemask_lt());
+    }
+    return 0u;
+  }
+  if (!valid) return 0u;
+  if constexpr (RET)
+    return atomicAdd(&wh[d], 1u);
+  atomicAdd(&wh[d], 1u);
+  return 0u;
+}
+
+// Peer mask of an RB-bit digit: the lanes holding the same digit as this lane
+// (RB ballots; every lane of the warp takes part).
+__device__ __forceinline__ uint32_t match_digit(uint32_t d) {
+  uint32_t m = FULL;
+#pragma unroll
+  for (int b = 0; b < RB; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t bal = __ballot_sync(FULL, bit);
+    m &= bit ? bal : ~bal;
+  }
+  return m;
+}
+
+// Stable in-warp ranking of the warp-striped items of one warp (item i of
+// lane l is element i*32 + l of the warp's chunk, elements [vlo, vhi) are
+// valid, items i >= kpt are absent): rank[i] = the warp's running count of
+// the digit (kept in `wh`, this warp's private M counters) plus the number of
+// earlier lanes of the same item holding the same digit.  Full-warp
+// operations only.
 template <class K, int KPT>
-__device__ __forceinline__ void warp_rank(const K (&k)[KPT], uint32_t shift, uint32_t wvalid,
-                                          uint32_t* wh, uint32_t (&rank)[KPT]) {
+__device__ __forceinline__ void warp_rank_stable(const K (&k)[KPT], uint32_t shift, uint32_t vlo, uint32_t vhi,
+                                                 uint32_t kpt, uint32_t* wh, uint32_t (&rank)[KPT]) {
   const uint32_t lane = lane_id();
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < KPT; ++i) {
-    const bool valid = (uint32_t)(i * 32) + lane < wvalid;
-    const uint32_t active = __ballot_sync(FULL, valid);
-    if (valid) {
+    if ((uint32_t)i < kpt) {
+      const uint32_t e = (uint32_t)(i * 32) + lane;
+      const bool valid = e >= vlo && e < vhi;
+      const uint32_t vmask = __ballot_sync(FULL, valid);
       const uint32_t d = digit_of(k[i], shift);
-      const uint32_t peers = __match_any_sync(active, d);
-      const uint32_t leader = 31u - (uint32_t)__clz((int)peers);
+      const uint32_t peers = match_digit(d) & vmask;
+      const uint32_t before = valid ? wh[d] : 0u;
+      __syncwarp();
       const uint32_t below = (uint32_t)__popc(peers & lt);
-      uint32_t base = 0;
-      if (lane == leader) base = atomicAdd(&wh[d], below + 1u);
-      base = __shfl_sync(peers, base, (int)leader);
-      rank[i] = base + below;
+      if (valid && below == 0u) wh[d] = before + (uint32_t)__popc(peers);
+      __syncwarp();
+      rank[i] = before + below;
     }
   }
 }
 
-// Visit the keys src[lo, hi) with every thread of the block, using 128-bit
-// loads for the 16-byte-aligned body.  f(key, valid) is called with
-// warp-uniform control flow (invalid lanes pass valid == false).
-template <class K, int NT, class F>
-__device__ __forceinline__ void block_visit(const K* src, uint32_t lo, uint32_t hi, F&& f) {
-  constexpr uint32_t VK = 16 / sizeof(K);
-  const K* p = src + lo;
-  const uint32_t n = hi - lo;
-  uint32_t head = (uint32_t)(((16u - ((uint32_t)(uintptr_t)p & 15u)) & 15u) / sizeof(K));
-  if (head > n) head = n;
-  {
-    const bool valid = threadIdx.x < head;
-    const K k = valid ? p[threadIdx.x] : K(0);
-    f(k, valid);
+// Block-wide OR of two values; the result is valid in every thread.  `sh`
+// holds 2 * (NT / 32) values of K.  Synchronises twice.
+template <class K, int NT>
+__device__ __forceinline__ void block_or2(K& a, K& b, K* sh) {
+  a = warp_or(a);
+  b = warp_or(b);
+  if (lane_id() == 0) {
+    sh[threadIdx.x >> 5] = a;
+    sh[NT / 32 + (threadIdx.x >> 5)] = b;
   }
-  const uint32_t nv = (n - head) / VK;
-  const uint4* pv = reinterpret_cast<const uint4*>(p + head);
-  for (uint32_t b = 0; b < nv; b += NT) {
-    const uint32_t v = b + threadIdx.x;
-    const bool valid = v < nv;
-    uint4 x = make_uint4(0u, 0u, 0u, 0u);
-    if (valid) x = __ldcs(pv + v);
-    if constexpr (sizeof(K) == 4) {
-      f((K)x.x, valid);
-      f((K)x.y, valid);
-      f((K)x.z, valid);
-      f((K)x.w, valid);
-    } else {
-      f((K)(((unsigned long long)x.y << 32) | x.x), valid);
-      f((K)(((unsigned long long)x.w << 32) | x.z), valid);
-    }
+  __syncthreads();
+  K x = 0, y = 0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) {
+    x |= sh[w];
+    y |= sh[NT / 32 + w];
   }
-  {
-    const uint32_t start = head + nv * VK;
-    const uint32_t rem = n - start;
-    const bool valid = threadIdx.x < rem;
-    const K k = valid ? p[start + threadIdx.x] : K(0);
-    f(k, valid);
-  }
+  __syncthreads();
+  a = x;
+  b = y;
 }
 
 // Stable sort of len <= 32 records by one warp (insertion-sort semantics:
@@ -346,6 +411,33 @@ __device__ __forceinline__ void warp_sort_tiny(const K* src, const uint32_t* vsr
   }
 }
 
+// Tiles of a segment start at its first key rounded down to a 16-byte
+// boundary, so that full tiles can be read with 128-bit loads; the first and
+// the last tile are partial.
+template <class K>
+__device__ __forceinline__ uint32_t tile_base(uint32_t off) {
+  return off & ~(uint32_t)(16 / sizeof(K) - 1);
+}
+template <class K, int TILE>
+__device__ __forceinline__ uint32_t seg_tiles(uint32_t off, uint32_t len) {
+  return (off + len - tile_base<K>(off) + (uint32_t)TILE - 1) / (uint32_t)TILE;
+}
+
+// Digit width for a segment of `len` keys whose varying bits all lie below
+// bit `top1`, partitioned at level L of `nlev` launched levels: wide enough
+// that its buckets come out near TCTA/2 keys (the radix adapts to the segment
+// size), and at least ceil(top1 / levels left) so the remaining levels always
+// consume every bit; at most RB.
+template <int TCTA>
+__device__ __forceinline__ uint32_t window_bits(uint32_t len, uint32_t top1, int L, uint32_t nlev) {
+  uint32_t b = 1;
+  while (b < (uint32_t)RB && (len >> b) > (uint32_t)(TCTA / 2)) ++b;
+  const uint32_t left = nlev > (uint32_t)L ? nlev - (uint32_t)L : 1u;
+  const uint32_t bmin = (top1 + left - 1) / left;
+  if (b < bmin) b = bmin;
+  return b > (uint32_t)RB ? (uint32_t)RB : b;
+}
+
 // ------------------------------------------------------------------ kernels
 
 // Zero the control block and the per-array root accumulators; for a plain
@@ -365,20 +457,117 @@ __global__ void k_init(Ctx c, ArrDesc a0, int write_a0, uint32_t root_words) {
   if (write_a0 && blockIdx.x == 0 && threadIdx.x == 0) c.arrs[0] = a0;
 }
 
+// Warp-level streaming count over keys src[lo, hi): 128-bit loads (batches
+// of 8 vectors per lane in flight), warp-aggregated increments of the warp's
+// private counters `wh` at digit (key >> shift) & (M-1) when do_hist, and
+// OR / NOT-AND of the keys into orv / nandv.
+template <class K>
+__device__ __forceinline__ void warp_count_range(const K* src, uint32_t lo, uint32_t hi, uint32_t shift,
+                                                 bool do_hist, uint32_t* wh, K& orv, K& nandv) {
+  constexpr uint32_t VK = 16 / sizeof(K);
+  constexpr int BATCH = 8;
+  const uint32_t lane = lane_id();
+  const K* p = src + lo;
+  const uint32_t n = hi - lo;
+  uint32_t head = (uint32_t)(((16u - ((uint32_t)(uintptr_t)p & 15u)) & 15u) / sizeof(K));
+  if (head > n) head = n;
+  auto one = [&](K k, bool valid) {
+    if (valid) {
+      orv |= k;
+      nandv |= ~k;
+    }
+    if (do_hist) warp_inc<false>(wh, digit_of(k, shift), valid);
+  };
+  {
+    const bool valid = lane < head;
+    one(valid ? p[lane] : K(0), valid);
+  }
+  const uint32_t nv = (n - head) / VK;
+  const uint4* pv = reinterpret_cast<const uint4*>(p + head);
+  for (uint32_t b = 0; b < nv; b += 32u * BATCH) {
+    uint4 x[BATCH];
+#pragma unroll
+    for (int q = 0; q < BATCH; ++q) {
+      const uint32_t v = b + (uint32_t)q * 32u + lane;
+      x[q] = v < nv ? __ldcs(pv + v) : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int q = 0; q < BATCH; ++q) {
+      const bool valid = b + (uint32_t)q * 32u + lane < nv;
+      if constexpr (sizeof(K) == 4) {
+        one((K)x[q].x, valid);
+        one((K)x[q].y, valid);
+        one((K)x[q].z, valid);
+        one((K)x[q].w, valid);
+      } else {
+        one((K)(((unsigned long long)x[q].y << 32) | x[q].x), valid);
+        one((K)(((unsigned long long)x[q].w << 32) | x[q].z), valid);
+      }
+    }
+  }
+  {
+    const uint32_t start = head + nv * VK;
+    const uint32_t rem = n - start;
+    const bool valid = lane < rem;
+    one(valid ? p[start + lane] : K(0), valid);
+  }
+}
+
+// Add a warp's private counters into a global histogram and clear them.
+__device__ __forceinline__ void warp_flush_hist(uint32_t* wh, uint32_t* gh) {
+  const uint32_t lane = lane_id();
+#pragma unroll
+  for (int i = 0; i < M / 32; ++i) {
+    const uint32_t x = wh[i * 32 + lane];
+    if (x) {
+      atomicAdd(&gh[i * 32 + lane], x);
+      wh[i * 32 + lane] = 0u;
+    }
+  }
+  __syncwarp();
+}
+
+template <class K>
+__device__ __forceinline__ void atomic_or_key(K* p, K v) {
+  if constexpr (sizeof(K) == 8)
+    atomicOr(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+  else
+    atomicOr(reinterpret_cast<uint32_t*>(p), (uint32_t)v);
+}
+
 // Root count: one read of every key; per array the OR / NOT-AND of its keys
 // and the histogram of its top byte (the initial counting pass, Alg. 1).
+// Every warp claims whole tiles on its own and keeps private counters and
+// OR/NOT-AND registers, flushed only when its next tile belongs to another
+// array -- no block-wide barrier.
 template <class K, int NT, int TILE>
 __global__ void __launch_bounds__(NT) k_root_count(Ctx c, uint32_t root_tiles) {
-  __shared__ uint32_t s_h[M];
-  __shared__ uint32_t s_t;
-  __shared__ K s_or[NT / 32], s_nand[NT / 32];
-  RootAcc<K>* root = reinterpret_cast<RootAcc<K>*>(c.root);
+  constexpr int NW = NT / 32;
   constexpr uint32_t TOP = 8 * sizeof(K) - RB;
+  __shared__ uint32_t s_h[NW * M];
+  RootAcc<K>* root = reinterpret_cast<RootAcc<K>*>(c.root);
+  const uint32_t lane = lane_id();
+  uint32_t* wh = s_h + (threadIdx.x >> 5) * M;
+#pragma unroll
+  for (int i = 0; i < M / 32; ++i) wh[i * 32 + lane] = 0u;
+  __syncwarp();
+  uint32_t cur = 0xffffffffu;
+  K orv = 0, nandv = 0;
+  auto flush = [&]() {
+    if (cur == 0xffffffffu) return;
+    warp_flush_hist(wh, root[cur].hist);
+    const K o = warp_or(orv), na = warp_or(nandv);
+    if (lane == 0) {
+      atomic_or_key(&root[cur].orv, o);
+      atomic_or_key(&root[cur].nand, na);
+    }
+    orv = 0;
+    nandv = 0;
+  };
   for (;;) {
-    if (threadIdx.x == 0) s_t = atomicAdd(&c.ctl->root_claim, 1u);
-    for (uint32_t i = threadIdx.x; i < M; i += NT) s_h[i] = 0;
-    __syncthreads();
-    const uint32_t t = s_t;
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&c.ctl->root_claim, 1u);
+    t = __shfl_sync(FULL, t, 0);
     if (t >= root_tiles) break;
     uint32_t lo = 0, hi = c.narr - 1;
     while (lo < hi) {
@@ -388,44 +577,21 @@ __global__ void __launch_bounds__(NT) k_root_count(Ctx c, uint32_t root_tiles) {
       else
         hi = mid - 1;
     }
+    if (lo != cur) {
+      flush();
+      cur = lo;
+    }
     const ArrDesc ad = c.arrs[lo];
     const uint32_t j = t - ad.root_tile_start;
     const uint32_t b = j * (uint32_t)TILE;
     const uint32_t e = min(ad.n, b + (uint32_t)TILE);
-    K orv = 0, nandv = 0;
-    block_visit<K, NT>(reinterpret_cast<const K*>(ad.keys), b, e, [&](K k, bool valid) {
-      if (valid) {
-        orv |= k;
-        nandv |= ~k;
-      }
-      hist_add(s_h, (uint32_t)(k >> TOP), valid);
-    });
-    orv = warp_or(orv);
-    nandv = warp_or(nandv);
-    if (lane_id() == 0) {
-      s_or[threadIdx.x >> 5] = orv;
-      s_nand[threadIdx.x >> 5] = nandv;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      K o = 0, na = 0;
-      for (int w = 0; w < NT / 32; ++w) {
-        o |= s_or[w];
-        na |= s_nand[w];
-      }
-      atomic_or_k(reinterpret_cast<std::conditional_t<sizeof(K) == 8, unsigned long long, uint32_t>*>(&root[lo].orv),
-                  o);
-      atomic_or_k(reinterpret_cast<std::conditional_t<sizeof(K) == 8, unsigned long long, uint32_t>*>(&root[lo].nand),
-                  na);
-    }
-    for (uint32_t i = threadIdx.x; i < M; i += NT)
-      if (s_h[i]) atomicAdd(&root[lo].hist[i], s_h[i]);
-    __syncthreads();
+    warp_count_range<K>(reinterpret_cast<const K*>(ad.keys), b, e, TOP, true, wh, orv, nandv);
   }
+  flush();
 }
 
 // Root classification, one CTA (256 threads) per array.
-template <class K, class V, int TILE, int TCTA>
+template <class K, class V, int TILE, int TCTA, int WCAP>
 __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long n_total) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr int W = 8 * sizeof(K);
@@ -463,11 +629,12 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
     }
     if (n <= (uint32_t)TCTA) {
       if (threadIdx.x == 0) {
-        const uint32_t q = atomicAdd(&ctl->cta_count, 1u);
-        if (q < c.ctacap) {
-          c.cta_q[q] = Item{0u, n, a, 0u};
-          atomicAdd(&ctl->cta_buckets, 1ull);
-          atomicAdd(&ctl->cta_keys, (unsigned long long)n);
+        const bool small = n <= (uint32_t)WCAP;
+        const uint32_t q = atomicAdd(small ? &ctl->wq_count : &ctl->cta_count, 1u);
+        if (q < (small ? c.wqcap : c.ctacap)) {
+          (small ? c.w_q : c.cta_q)[q] = Item{0u, n, a, 0u};
+          atomicAdd(small ? &ctl->wsort_buckets : &ctl->cta_buckets, 1ull);
+          atomicAdd(small ? &ctl->wsort_keys : &ctl->cta_keys, (unsigned long long)n);
         } else {
           atomicOr(&ctl->err, DERR_CAPACITY);
         }
@@ -475,20 +642,24 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
       continue;
     }
     const int hb = top_bit<K>(orv ^ andv);
+    const uint32_t b = window_bits<TCTA>(n, (uint32_t)hb + 1u, 0, c.nlev);
+    const uint32_t shift0 = (uint32_t)hb + 1u > b ? (uint32_t)hb + 1u - b : 0u;
+    // a window inside the top byte reuses the root histogram (coarsened)
     const bool use_top = hb >= W - RB;
-    const uint32_t shift = use_top ? (uint32_t)(W - RB) : (uint32_t)(hb >= RB - 1 ? hb - (RB - 1) : 0);
+    const uint32_t shift = use_top ? max(shift0, (uint32_t)(W - RB)) : shift0;
+    const uint32_t bits = (uint32_t)hb + 1u - shift;
     const uint32_t nt = (n + TILE - 1) / TILE;
     if (threadIdx.x == 0) {
       const uint32_t s = atomicAdd(&ctl->lv[0].nseg, 1u);
       const uint32_t ts = atomicAdd(&ctl->lv[0].ntiles, nt);
       s_ok = (s < c.segcap && ts + nt <= c.tilecap) ? 1u : 0u;
       if (s_ok) {
-        c.segs[0][s] = Seg{0u, n, a, ts, shift, 0u, use_top ? 0u : SEG_NEEDS_HIST, 0u};
-        atomicAdd(&ctl->lv[0].keys, (unsigned long long)n);
+        c.segs[0][s] = Seg{0u, n, a, ts, shift, 0u, use_top ? 0u : SEG_NEEDS_HIST, bits,
+                           (unsigned long long)root[a].nand, (unsigned long long)orv};
       } else {
         // Cannot happen with the workspace bounds; stay consistent anyway.
         atomicOr(&ctl->err, DERR_CAPACITY);
-        if (s < c.segcap) c.segs[0][s] = Seg{0u, 0u, a, 0u, 0u, 0u, 0u, 0u};
+        if (s < c.segcap) c.segs[0][s] = Seg{0u, 0u, a, 0u, 0u, 0u, 0u, 0u, 0ull, 0ull};
       }
       s_seg = s;
       s_ts = ts;
@@ -496,7 +667,17 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
     __syncthreads();
     {
       const uint32_t s = s_seg, ts = s_ts;
-      if (s < c.segcap) c.hist[0][(size_t)s * M + threadIdx.x] = (s_ok && use_top) ? root[a].hist[threadIdx.x] : 0u;
+      if (s < c.segcap) {
+        uint32_t h = 0;
+        if (s_ok && use_top) {
+          // digit (key >> shift) & 255 = top byte >> (shift - (W - RB))
+          const uint32_t sd = shift - (uint32_t)(W - RB);
+          const uint32_t x = threadIdx.x;
+          if ((x << sd) < (uint32_t)M)
+            for (uint32_t y = x << sd; y < ((x + 1) << sd); ++y) h += root[a].hist[y];
+        }
+        c.hist[0][(size_t)s * M + threadIdx.x] = h;
+      }
       const uint32_t owner = s_ok ? s : NO_OWNER;
       const uint32_t ntc = ts < c.tilecap ? min(nt, c.tilecap - ts) : 0u;
       for (uint32_t i = threadIdx.x; i < ntc; i += 256) c.tile_owner[ts + i] = owner;
@@ -505,102 +686,161 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
   }
 }
 
-// Level count: histogram of each segment's digit (when the root count does not
-// already hold it), plus resetting the look-back words of every tile and the
-// AND/OR accumulators of every segment of this level.
+// Level count: per segment of this level, the histogram of its digit window
+// (unless the root count already holds it) and the AND/OR of its keys (unless
+// known); it also resets the look-back words of every tile of the level.
+// Warp-granular like k_root_count: private counters flushed per segment.
 template <class K, int NT, int TILE>
 __global__ void __launch_bounds__(NT) k_level_count(Ctx c, int L) {
-  __shared__ uint32_t s_h[M];
-  __shared__ uint32_t s_t;
+  constexpr int NW = NT / 32;
+  __shared__ uint32_t s_h[NW * M];
   LevelCtl* lc = &c.ctl->lv[L];
   const uint32_t ntiles = min(lc->ntiles, c.tilecap);
-  const Seg* segs = c.segs[L & 1];
-  uint32_t* hist = c.hist[L & 1];
-  K* a_or = reinterpret_cast<K*>(c.a_or);
-  K* a_nand = reinterpret_cast<K*>(c.a_nand);
-  for (;;) {
-    if (threadIdx.x == 0) s_t = atomicAdd(&lc->hist_claim, 1u);
-    for (uint32_t i = threadIdx.x; i < M; i += NT) s_h[i] = 0;
-    __syncthreads();
-    const uint32_t t = s_t;
-    if (t >= ntiles) break;
-    const uint32_t s = c.tile_owner[t];
-    for (uint32_t i = threadIdx.x; i < M; i += NT) c.status[(size_t)t * M + i] = 0u;
-    if (s >= c.segcap) {
-      __syncthreads();
-      continue;
-    }
-    const Seg seg = segs[s];
-    const uint32_t j = t - seg.tile_start;
-    if (j == 0) {
-      for (uint32_t i = threadIdx.x; i < M; i += NT) {
-        a_or[(size_t)s * M + i] = K(0);
-        a_nand[(size_t)s * M + i] = K(0);
+  Seg* segs = ((L & 1) ? c.segs[1] : c.segs[0]);
+  uint32_t* hist = ((L & 1) ? c.hist[1] : c.hist[0]);
+  const uint32_t lane = lane_id();
+  uint32_t* wh = s_h + (threadIdx.x >> 5) * M;
+#pragma unroll
+  for (int i = 0; i < M / 32; ++i) wh[i * 32 + lane] = 0u;
+  __syncwarp();
+  uint32_t cur = 0xffffffffu, cur_flags = 0u;
+  unsigned long long keys_read = 0;
+  K orv = 0, nandv = 0;
+  auto flush = [&]() {
+    if (cur == 0xffffffffu) return;
+    if (cur_flags & SEG_NEEDS_HIST) warp_flush_hist(wh, hist + (size_t)cur * M);
+    if (cur_flags & SEG_NEEDS_ANDOR) {
+      const K o = warp_or(orv), na = warp_or(nandv);
+      if (lane == 0) {
+        atomic_or_u64(&segs[cur].orv, (unsigned long long)o);
+        atomic_or_u64(&segs[cur].nand, (unsigned long long)na);
       }
     }
-    if (seg.flags & SEG_NEEDS_HIST) {
-      const ArrDesc ad = c.arrs[seg.arr];
-      const K* src = reinterpret_cast<const K*>(seg.parity ? ad.buf : ad.keys);
-      const uint32_t b = seg.off + j * (uint32_t)TILE;
-      const uint32_t e = min(seg.off + seg.len, b + (uint32_t)TILE);
-      const uint32_t shift = seg.shift;
-      block_visit<K, NT>(src, b, e, [&](K k, bool valid) { hist_add(s_h, digit_of(k, shift), valid); });
-      __syncthreads();
-      for (uint32_t i = threadIdx.x; i < M; i += NT)
-        if (s_h[i]) atomicAdd(&hist[(size_t)s * M + i], s_h[i]);
-      if (threadIdx.x == 0) atomicAdd(&lc->hist_keys, (unsigned long long)(e - b));
+    orv = 0;
+    nandv = 0;
+  };
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&lc->hist_claim, 1u);
+    t = __shfl_sync(FULL, t, 0);
+    if (t >= ntiles) break;
+#pragma unroll
+    for (int i = 0; i < M / 32; ++i) c.status[(size_t)t * M + i * 32 + lane] = 0u;
+    const uint32_t s = c.tile_owner[t];
+    if (s >= c.segcap) continue;
+    const Seg seg = segs[s];
+    const uint32_t flags = seg.flags & (SEG_NEEDS_HIST | SEG_NEEDS_ANDOR);
+    if (!flags) continue;
+    if (s != cur) {
+      flush();
+      cur = s;
+      cur_flags = flags;
     }
-    __syncthreads();
+    const uint32_t j = t - seg.tile_start;
+    const ArrDesc ad = c.arrs[seg.arr];
+    const K* src = reinterpret_cast<const K*>(seg.parity ? ad.buf : ad.keys);
+    const uint32_t tb = tile_base<K>(seg.off) + j * (uint32_t)TILE;
+    const uint32_t b = max(tb, seg.off);
+    const uint32_t e = min(seg.off + seg.len, tb + (uint32_t)TILE);
+    warp_count_range<K>(src, b, e, seg.shift, (flags & SEG_NEEDS_HIST) != 0u, wh, orv, nandv);
+    keys_read += e - b;
   }
+  flush();
+  if (lane == 0 && keys_read) atomicAdd(&lc->hist_keys, keys_read);
 }
 
 template <class K, class V, int NT, int KPT>
 constexpr size_t scatter_smem_bytes() {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr size_t TILE = (size_t)NT * KPT;
-  return TILE * sizeof(K) + (KV ? TILE * 4 : 0) + (size_t)(NT / 32) * M * 4 + 2 * M * 4 + 2 * M * sizeof(K);
+  // staging area; counters (per warp for the stable key-value ranking, one
+  // block-wide set otherwise); tile digit starts; global offsets
+  return TILE * sizeof(K) + (KV ? TILE * 4 : 0) + (KV ? (size_t)(NT / 32) * M * 4 : (size_t)M * 4) + 2 * M * 4;
 }
 
-// Scatter (deal) of one level: every tile of every segment is ranked in
-// shared memory, combined with earlier tiles of its segment by a single-pass
-// decoupled look-back per digit, staged in digit order and written to the
-// other buffer so that each digit's run is contiguous in HBM.
+// A segment is dealt at its level unless all its keys are equal or its digit
+// window holds no varying bit (then k_classify finishes or re-windows it).
+template <class K>
+__device__ __forceinline__ bool seg_is_dealt(const Seg& seg) {
+  const K vm = (K)seg.orv & (K)seg.nand;
+  return vm != K(0) && ((vm >> seg.shift) & (K)(M - 1)) != K(0);
+}
+
+// Decoupled look-back for digit d of tile t (one thread per digit): sums the
+// counts of the earlier tiles of the segment back to the first inclusive
+// prefix, then publishes this tile's inclusive prefix.  Every wait is bounded
+// by c.spin_limit; a wait that runs out records DERR_TIMEOUT and *fail.
+__device__ __forceinline__ uint32_t look_back(const Ctx& c, uint32_t t, uint32_t tile_start, uint32_t d,
+                                              uint32_t tcount, uint32_t* fail) {
+  uint32_t* st = c.status + (size_t)t * M;
+  uint32_t excl = 0;
+  if (t > tile_start) {
+    bool ok = true;
+    uint32_t tp = t - 1;
+    for (;;) {
+      const uint32_t* p = c.force_timeout ? &c.ctl->never : c.status + (size_t)tp * M + d;
+      uint32_t x = ld_relaxed(p);
+      uint32_t spins = 0;
+      while ((x >> 30) == 0u) {
+        if (++spins > c.spin_limit) break;
+        if (spins > 64) __nanosleep(64);
+        x = ld_relaxed(p);
+      }
+      if ((x >> 30) == 0u) {
+        ok = false;
+        break;
+      }
+      excl += x & COUNT_MASK;
+      if ((x & FLAG_INC) || tp == tile_start) break;
+      --tp;
+    }
+    if (!ok) {
+      record_error(c.ctl, DERR_TIMEOUT, ERR_SITE_LOOKBACK);
+      *fail = 1u;
+    }
+    st_relaxed(st + d, FLAG_INC | ((excl + tcount) & COUNT_MASK));
+  }
+  return excl;
+}
+
+// Scatter (deal) of one level: every tile of every dealt segment is ranked in
+// shared memory, combined with the earlier tiles of its segment by a
+// single-pass decoupled look-back per digit, staged in digit order and
+// written to the other buffer, so each digit's run is contiguous in HBM.
+// Key-only: one returning shared atomic per key on block-wide counters gives
+// each key a distinct slot of its digit (order among equal digits is free);
+// full tiles of 16-byte-aligned arrays are read with 128-bit loads.
+// Key-value: stable per-warp ranking in element order.
 template <class K, class V, int NT, int KPT>
 __global__ void __launch_bounds__(NT, 2) k_scatter(Ctx c, int L) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr uint32_t TILE = (uint32_t)NT * KPT;
   constexpr int NW = NT / 32;
-  using KA = std::conditional_t<sizeof(K) == 8, unsigned long long, uint32_t>;
+  constexpr uint32_t VK = 16 / sizeof(K);
+  static_assert(KV || KPT % VK == 0, "vector loads cover whole items");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   K* s_keys = reinterpret_cast<K*>(smem_raw);
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + TILE);
-  uint32_t* s_whist = s_vals + (KV ? TILE : 0);
-  uint32_t* s_tstart = s_whist + NW * M;
-  uint32_t* s_gstart = s_tstart + M;
-  K* s_or = reinterpret_cast<K*>(s_gstart + M);
-  K* s_nand = s_or + M;
+  uint32_t* s_cnt = s_vals + (KV ? TILE : 0);  // KV: [NW][M] per warp; else [M]
+  uint32_t* s_tstart = s_cnt + (KV ? NW * M : M);
+  uint32_t* s_goff = s_tstart + M;  // global destination of staged element e of digit d = s_goff[d] + e
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_t, s_fail;
 
   LevelCtl* lc = &c.ctl->lv[L];
   const uint32_t ntiles = min(lc->ntiles, c.tilecap);
-  const Seg* segs = c.segs[L & 1];
-  const uint32_t* hist = c.hist[L & 1];
-  K* a_or = reinterpret_cast<K*>(c.a_or);
-  K* a_nand = reinterpret_cast<K*>(c.a_nand);
+  const Seg* segs = ((L & 1) ? c.segs[1] : c.segs[0]);
+  const uint32_t* hist = ((L & 1) ? c.hist[1] : c.hist[0]);
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  uint32_t* wh = s_whist + warp * M;
 
+  // Tiles are claimed in increasing order by running CTAs only, so the tile a
+  // look-back waits for is always being processed by some resident CTA.
   for (;;) {
     if (threadIdx.x == 0) {
       s_t = atomicAdd(&lc->scat_claim, 1u);
       s_fail = 0u;
     }
-    for (uint32_t i = threadIdx.x; i < (uint32_t)(NW * M); i += NT) s_whist[i] = 0u;
-    for (uint32_t i = threadIdx.x; i < M; i += NT) {
-      s_or[i] = K(0);
-      s_nand[i] = K(0);
-    }
+    for (uint32_t i = threadIdx.x; i < (uint32_t)(KV ? NW * M : M); i += NT) s_cnt[i] = 0u;
     __syncthreads();
     const uint32_t t = s_t;
     if (t >= ntiles) break;
@@ -610,143 +850,155 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Ctx c, int L) {
       continue;
     }
     const Seg seg = segs[s];
+    if (!seg_is_dealt<K>(seg)) {
+      __syncthreads();
+      continue;
+    }
     const ArrDesc ad = c.arrs[seg.arr];
     const K* src = reinterpret_cast<const K*>(seg.parity ? ad.buf : ad.keys);
     K* dst = reinterpret_cast<K*>(seg.parity ? ad.keys : ad.buf);
     const uint32_t* vsrc = reinterpret_cast<const uint32_t*>(seg.parity ? ad.vbuf : ad.vals);
     uint32_t* vdst = reinterpret_cast<uint32_t*>(seg.parity ? ad.vals : ad.vbuf);
     const uint32_t j = t - seg.tile_start;
-    const uint32_t tb = seg.off + j * TILE;
-    const uint32_t cnt = min(TILE, seg.off + seg.len - tb);
+    const uint32_t tb = tile_base<K>(seg.off) + j * TILE;         // first element of the tile
+    const uint32_t seg_end = seg.off + seg.len;
+    const uint32_t vlo = seg.off > tb ? seg.off - tb : 0u;         // valid elements: [vlo, vhi)
+    const uint32_t vhi = min(TILE, seg_end - tb);
+    const uint32_t nvalid = vhi - vlo;
     const uint32_t shift = seg.shift;
-    const uint32_t wb = warp * 32u * KPT;
-    const uint32_t wvalid = cnt > wb ? min(cnt - wb, 32u * KPT) : 0u;
 
     K k[KPT];
     uint32_t r[KPT];
     uint32_t v[KV ? KPT : 1];
+    if constexpr (KV) {
+      // warp-striped: item i of lane l is element wb + i*32 + l
+      const uint32_t wb = warp * 32u * KPT;
 #pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-      const uint32_t e = (uint32_t)(i * 32) + lane;
-      if (e < wvalid) {
-        k[i] = ld_stream(src + tb + wb + e);
-        if constexpr (KV) v[i] = ld_stream(vsrc + tb + wb + e);
-      } else {
+      for (int i = 0; i < KPT; ++i) {
+        const uint32_t e = wb + (uint32_t)(i * 32) + lane;
         k[i] = K(0);
+        if (e >= vlo && e < vhi) {
+          k[i] = ld_stream(src + tb + e);
+          v[i] = ld_stream(vsrc + tb + e);
+        }
       }
-      r[i] = 0u;
+      uint32_t* wh = s_cnt + warp * M;
+      const uint32_t wlo = vlo > wb ? vlo - wb : 0u;
+      const uint32_t whi = vhi > wb ? min(vhi - wb, 32u * KPT) : 0u;
+      warp_rank_stable<K, KPT>(k, shift, wlo, whi, KPT, wh, r);
+    } else {
+      // item i = VK * q + u of thread x is element VK * (q * NT + x) + u
+      const bool vec = ((((uintptr_t)src) & 15u) == 0u) && tb + TILE <= ad.n;
+      if (vec) {
+        const uint4* pv = reinterpret_cast<const uint4*>(src + tb);
+#pragma unroll
+        for (int q = 0; q < KPT / (int)VK; ++q) {
+          const uint4 x = __ldcs(pv + q * NT + threadIdx.x);
+          if constexpr (sizeof(K) == 4) {
+            k[q * 4 + 0] = (K)x.x;
+            k[q * 4 + 1] = (K)x.y;
+            k[q * 4 + 2] = (K)x.z;
+            k[q * 4 + 3] = (K)x.w;
+          } else {
+            k[q * 2 + 0] = (K)(((unsigned long long)x.y << 32) | x.x);
+            k[q * 2 + 1] = (K)(((unsigned long long)x.w << 32) | x.z);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < KPT; ++i) {
+          const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
+          k[i] = (e >= vlo && e < vhi) ? src[tb + e] : K(0);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < KPT; ++i) {
+        const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
+        r[i] = warp_inc<true>(s_cnt, digit_of(k[i], shift), e >= vlo && e < vhi);
+      }
     }
-    warp_rank<K, KPT>(k, shift, wvalid, wh, r);
     __syncthreads();
 
-    // Per digit: tile count, and per-warp counts turned into exclusive offsets.
+    // Per digit: tile count (KV: per-warp counts become exclusive offsets).
     uint32_t tcount = 0;
     if (threadIdx.x < M) {
-      for (int w2 = 0; w2 < NW; ++w2) {
-        const uint32_t x = s_whist[w2 * M + threadIdx.x];
-        s_whist[w2 * M + threadIdx.x] = tcount;
-        tcount += x;
+      if constexpr (KV) {
+        for (int w2 = 0; w2 < NW; ++w2) {
+          const uint32_t x = s_cnt[w2 * M + threadIdx.x];
+          s_cnt[w2 * M + threadIdx.x] = tcount;
+          tcount += x;
+        }
+      } else {
+        tcount = s_cnt[threadIdx.x];
       }
+      st_relaxed(c.status + (size_t)t * M + threadIdx.x, (j == 0 ? FLAG_INC : FLAG_AGG) | tcount);
     }
-    uint32_t* st = c.status + (size_t)t * M;
-    if (threadIdx.x < M) st_relaxed(st + threadIdx.x, (j == 0 ? FLAG_INC : FLAG_AGG) | tcount);
     const uint32_t tstart = scan256(tcount, s_scan, nullptr);
     const uint32_t hcount = threadIdx.x < M ? hist[(size_t)s * M + threadIdx.x] : 0u;
     const uint32_t bexcl = scan256(hcount, s_scan, nullptr);
-
     if (threadIdx.x < M) {
-      uint32_t excl = 0;
-      if (j > 0) {
-        bool ok = true;
-        uint32_t tp = t - 1;
-        for (;;) {
-          const uint32_t* p = c.force_timeout ? &c.ctl->never : c.status + (size_t)tp * M + threadIdx.x;
-          uint32_t x = ld_relaxed(p);
-          uint32_t spins = 0;
-          while ((x >> 30) == 0u) {
-            if (++spins > c.spin_limit) break;
-            if (spins > 64) __nanosleep(64);
-            x = ld_relaxed(p);
-          }
-          if ((x >> 30) == 0u) {
-            ok = false;
-            break;
-          }
-          excl += x & COUNT_MASK;
-          if ((x & FLAG_INC) || tp == seg.tile_start) break;
-          --tp;
-        }
-        if (!ok) {
-          atomicOr(&c.ctl->err, DERR_TIMEOUT);
-          s_fail = 1u;
-        }
-        st_relaxed(st + threadIdx.x, FLAG_INC | ((excl + tcount) & COUNT_MASK));
-      }
+      const uint32_t excl = look_back(c, t, seg.tile_start, threadIdx.x, tcount, &s_fail);
       s_tstart[threadIdx.x] = tstart;
-      s_gstart[threadIdx.x] = seg.off + bexcl + excl;
+      s_goff[threadIdx.x] = seg.off + bexcl + excl - tstart;
     }
     __syncthreads();
 
-    // Stage the tile in shared memory in stable digit order.
+    // Stage the tile in shared memory in digit order.
 #pragma unroll
     for (int i = 0; i < KPT; ++i) {
-      if ((uint32_t)(i * 32) + lane < wvalid) {
-        const uint32_t d = digit_of(k[i], shift);
-        const uint32_t pos = s_tstart[d] + wh[d] + r[i];
-        if (pos < cnt) {
+      bool valid;
+      uint32_t pos;
+      const uint32_t d = digit_of(k[i], shift);
+      if constexpr (KV) {
+        const uint32_t e = warp * 32u * KPT + (uint32_t)(i * 32) + lane;
+        valid = e >= vlo && e < vhi;
+        pos = s_tstart[d] + s_cnt[warp * M + d] + r[i];
+      } else {
+        const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
+        valid = e >= vlo && e < vhi;
+        pos = s_tstart[d] + r[i];
+      }
+      if (valid) {
+        if (pos < nvalid) {
           s_keys[pos] = k[i];
           if constexpr (KV) s_vals[pos] = v[i];
         } else {
-          atomicOr(&c.ctl->err, DERR_BOUNDS);
+          record_error(c.ctl, DERR_BOUNDS, ERR_SITE_SCATTER_STAGE);
         }
       }
     }
     __syncthreads();
 
-    // Coalesced write-out; fold the AND/OR of every destination bucket.
-    const bool fail = s_fail != 0u;
-    const uint32_t seg_end = seg.off + seg.len;
-    for (uint32_t b0 = 0; b0 < cnt; b0 += NT) {
-      const uint32_t e = b0 + threadIdx.x;
-      const bool valid = e < cnt;
-      const K kk = valid ? s_keys[e] : K(0);
-      const uint32_t d = digit_of(kk, shift);
-      if (valid && !fail) {
-        const uint32_t g = s_gstart[d] + (e - s_tstart[d]);
-        if (g >= seg.off && g < seg_end) {
+    // Coalesced write-out of the staged runs.
+    if (s_fail == 0u) {
+#pragma unroll 4
+      for (uint32_t e = threadIdx.x; e < nvalid; e += NT) {
+        const K kk = s_keys[e];
+        const uint32_t g = s_goff[digit_of(kk, shift)] + e;
+        if (g - seg.off < seg.len) {
           dst[g] = kk;
           if constexpr (KV) vdst[g] = s_vals[e];
         } else {
-          atomicOr(&c.ctl->err, DERR_BOUNDS);
+          record_error(c.ctl, DERR_BOUNDS, ERR_SITE_SCATTER_WRITE);
         }
       }
-      const uint32_t active = __ballot_sync(FULL, valid);
-      if (valid) {
-        const uint32_t peers = __match_any_sync(active, d);
-        const K o = group_or<K>(peers, kk);
-        const K na = group_or<K>(peers, ~kk);
-        if (lane == (uint32_t)(__ffs(peers) - 1)) {
-          atomic_or_k(reinterpret_cast<KA*>(&s_or[d]), (KA)o);
-          atomic_or_k(reinterpret_cast<KA*>(&s_nand[d]), (KA)na);
-        }
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < M && tcount > 0) {
-      atomic_or_k(reinterpret_cast<KA*>(&a_or[(size_t)s * M + threadIdx.x]), (KA)s_or[threadIdx.x]);
-      atomic_or_k(reinterpret_cast<KA*>(&a_nand[(size_t)s * M + threadIdx.x]), (KA)s_nand[threadIdx.x]);
     }
     __syncthreads();
   }
 }
 
-enum : uint32_t { CLS_NONE = 0, CLS_DONE, CLS_TINY_SORT, CLS_TINY_COPY, CLS_CTA_SORT, CLS_CTA_COPY, CLS_BIG, CLS_BIG_COPY };
+enum : uint32_t {
+  CLS_NONE = 0, CLS_DONE, CLS_TINY_SORT, CLS_TINY_COPY, CLS_WARP_SORT, CLS_CTA_SORT, CLS_BIG, CLS_BIG_COPY
+};
 
-// Classification of the buckets of one level, one CTA (256 threads = one per
-// digit) per segment: diversion decision by bucket size (threshold N_d,
-// Section "Analysis"), constant buckets finished (Section MSD), tiny buckets
-// sorted here by warps, large buckets turned into next-level segments.
-template <class K, class V, int TILE, int TCTA>
+// Classification of one level, one CTA (256 threads = one per digit) per
+// segment.  A constant segment is finished (copied back if it sits in the
+// buffer); a segment whose window held no varying bit is passed to the next
+// level with its window at the highest varying bit, without moving data; for
+// a dealt segment every bucket is classified by size against the diversion
+// thresholds (Section "Analysis", N_d): tiny buckets are sorted here by warps,
+// mid-size ones queued for k_ctasort, large ones become next-level segments.
+template <class K, class V, int TILE, int TCTA, int WCAP>
 __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   __shared__ uint32_t s_scan[8];
@@ -755,120 +1007,168 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
   // New next-level segments / large copy items of this segment: owner value
   // for their tile range, histogram slot to clear, first tile, tile count.
   __shared__ uint32_t s_new_owner[M], s_new_zero[M], s_new_ts[M], s_new_nt[M], s_new_copy[M];
-  __shared__ unsigned long long s_stat[8];
+  __shared__ unsigned long long s_stat[10];
   Ctl* ctl = c.ctl;
   const uint32_t nseg = min(ctl->lv[L].nseg, c.segcap);
-  const Seg* segs = c.segs[L & 1];
-  const uint32_t* hist = c.hist[L & 1];
-  const K* a_or = reinterpret_cast<const K*>(c.a_or);
-  const K* a_nand = reinterpret_cast<const K*>(c.a_nand);
+  const Seg* segs = ((L & 1) ? c.segs[1] : c.segs[0]);
+  const uint32_t* hist = ((L & 1) ? c.hist[1] : c.hist[0]);
   LevelCtl* ln = &ctl->lv[L + 1];
-  Seg* segs_n = c.segs[(L + 1) & 1];
-  uint32_t* hist_n = c.hist[(L + 1) & 1];
+  Seg* segs_n = ((L & 1) ? c.segs[0] : c.segs[1]);
+  uint32_t* hist_n = ((L & 1) ? c.hist[0] : c.hist[1]);
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t d = threadIdx.x;
 
+  // Append one next-level segment and record its tile range for the owner
+  // fill.  Called by one thread.
+  auto add_big = [&](uint32_t off, uint32_t cnt, uint32_t arr, uint32_t shift, uint32_t bits, uint32_t parity,
+                     uint32_t flags, unsigned long long nand, unsigned long long orv) {
+    const uint32_t nt = seg_tiles<K, TILE>(off, cnt);
+    const uint32_t s2 = atomicAdd(&ln->nseg, 1u);
+    const uint32_t ts = atomicAdd(&ln->ntiles, nt);
+    const bool ok = L + 1 < MAXLV && s2 < c.segcap && ts + nt <= c.tilecap;
+    if (ok) {
+      segs_n[s2] = Seg{off, cnt, arr, ts, shift, parity, flags, bits, nand, orv};
+    } else {
+      // Cannot happen with the workspace bounds; keep every slot consistent
+      // anyway: an empty segment and tiles nobody processes.
+      atomicOr(&ctl->err, DERR_CAPACITY);
+      if (s2 < c.segcap) segs_n[s2] = Seg{0u, 0u, arr, 0u, 0u, 0u, 0u, 0u, 0ull, 0ull};
+    }
+    const uint32_t i = atomicAdd(&s_new_n, 1u);
+    s_new_owner[i] = ok ? s2 : NO_OWNER;
+    s_new_zero[i] = s2 < c.segcap ? s2 : NO_OWNER;
+    s_new_ts[i] = ts;
+    s_new_nt[i] = ts < c.tilecap ? min(nt, c.tilecap - ts) : 0u;
+    s_new_copy[i] = 0u;
+  };
+  // Append one large copy item (constant keys in buf) and its tile range.
+  auto add_copy = [&](uint32_t off, uint32_t cnt, uint32_t arr, unsigned long long value) {
+    const uint32_t nt = (cnt + (uint32_t)TILE - 1) / (uint32_t)TILE;
+    const uint32_t q = atomicAdd(&ctl->copy_count, 1u);
+    const uint32_t ts = atomicAdd(&ctl->copy_tiles, nt);
+    const bool ok = q < c.copycap && ts + nt <= c.copytilecap;
+    if (ok)
+      c.copy_q[q] = CopyItem{off, cnt, arr, ts, value};
+    else
+      atomicOr(&ctl->err, DERR_CAPACITY);
+    const uint32_t i = atomicAdd(&s_new_n, 1u);
+    s_new_owner[i] = ok ? q : NO_OWNER;
+    s_new_zero[i] = NO_OWNER;
+    s_new_ts[i] = ts;
+    s_new_nt[i] = ts < c.copytilecap ? min(nt, c.copytilecap - ts) : 0u;
+    s_new_copy[i] = 1u;
+  };
+
   for (uint32_t s = blockIdx.x; s < nseg; s += gridDim.x) {
     const Seg seg = segs[s];
-    const uint32_t cnt = hist[(size_t)s * M + d];
-    const uint32_t excl = scan256(cnt, s_scan, nullptr);
     if (threadIdx.x == 0) {
       s_tiny_n = 0;
       s_new_n = 0;
     }
-    if (threadIdx.x < 8) s_stat[threadIdx.x] = 0ull;
+    if (threadIdx.x < 10) s_stat[threadIdx.x] = 0ull;
     __syncthreads();
-    const uint32_t off = seg.off + excl;
-    const uint32_t pout = seg.parity ^ 1u;
-    const K orv = a_or[(size_t)s * M + d];
-    const K andv = ~a_nand[(size_t)s * M + d];
-    uint32_t cls = CLS_NONE;
-    if (cnt == 0)
-      cls = CLS_NONE;
-    else if (cnt == 1 || orv == andv)
-      cls = !pout ? CLS_DONE : (cnt <= T_WARP ? CLS_TINY_COPY : (cnt <= (uint32_t)TCTA ? CLS_CTA_COPY : CLS_BIG_COPY));
-    else if (cnt <= T_WARP)
-      cls = CLS_TINY_SORT;
-    else if (cnt <= (uint32_t)TCTA)
-      cls = CLS_CTA_SORT;
-    else
-      cls = CLS_BIG;
-
-    // Mid-size buckets: warp-aggregated append to the CTA-sort queue.
-    const bool want = cls == CLS_CTA_SORT || cls == CLS_CTA_COPY;
-    const uint32_t wm = __ballot_sync(FULL, want);
-    if (wm) {
-      const uint32_t first = (uint32_t)(__ffs(wm) - 1);
-      uint32_t qb = 0;
-      if (lane == first) qb = atomicAdd(&ctl->cta_count, (uint32_t)__popc(wm));
-      qb = __shfl_sync(FULL, qb, (int)first);
-      if (want) {
-        const uint32_t q = qb + (uint32_t)__popc(wm & lanemask_lt());
-        if (q < c.ctacap)
-          c.cta_q[q] = Item{off, cnt, seg.arr, pout | (cls == CLS_CTA_COPY ? ITEM_COPY : 0u)};
-        else
-          atomicOr(&ctl->err, DERR_CAPACITY);
+    const K vm = (K)seg.orv & (K)seg.nand;
+    const bool dealt = vm != K(0) && ((vm >> seg.shift) & (K)(M - 1)) != K(0);
+    if (!dealt) {
+      if (threadIdx.x == 0 && seg.len > 0) {
+        if (vm == K(0)) {
+          // every key of the segment is equal: finished where it lies
+          s_stat[0] = 1ull;
+          s_stat[1] = seg.len;
+          if (seg.parity) {
+            s_stat[2] = seg.len;
+            if (seg.len <= (uint32_t)TCTA) {
+              const uint32_t q = atomicAdd(&ctl->cta_count, 1u);
+              if (q < c.ctacap)
+                c.cta_q[q] = Item{seg.off, seg.len, seg.arr, ITEM_PARITY | ITEM_COPY};
+              else
+                atomicOr(&ctl->err, DERR_CAPACITY);
+            } else {
+              add_copy(seg.off, seg.len, seg.arr, (unsigned long long)(K)seg.orv);
+            }
+          }
+        } else {
+          // the window held no varying bit: move it down to the highest one
+          const uint32_t top1 = (uint32_t)top_bit<K>(vm) + 1u;
+          const uint32_t b = window_bits<TCTA>(seg.len, top1, L + 1, c.nlev);
+          const uint32_t shift = top1 > b ? top1 - b : 0u;
+          add_big(seg.off, seg.len, seg.arr, shift, top1 - shift, seg.parity, SEG_NEEDS_HIST, seg.nand, seg.orv);
+        }
       }
-    }
-    if (cls == CLS_TINY_SORT || cls == CLS_TINY_COPY) {
-      const uint32_t i = atomicAdd(&s_tiny_n, 1u);
-      s_tiny_off[i] = off;
-      s_tiny_len[i] = cnt | (cls == CLS_TINY_COPY ? 0x80000000u : 0u);
-    }
-    if (cls == CLS_BIG) {
-      const uint32_t nt = (cnt + (uint32_t)TILE - 1) / (uint32_t)TILE;
-      const uint32_t s2 = atomicAdd(&ln->nseg, 1u);
-      const uint32_t ts = atomicAdd(&ln->ntiles, nt);
-      const bool ok = L + 1 < MAXLV && s2 < c.segcap && ts + nt <= c.tilecap;
-      if (ok) {
-        const int hb = top_bit<K>(orv ^ andv);
-        const uint32_t shift = (uint32_t)(hb >= RB - 1 ? hb - (RB - 1) : 0);
-        segs_n[s2] = Seg{off, cnt, seg.arr, ts, shift, pout, SEG_NEEDS_HIST, 0u};
-        atomicAdd(&ln->keys, (unsigned long long)cnt);
-      } else {
-        // Cannot happen with the workspace bounds; keep every slot consistent
-        // anyway: an empty segment and tiles nobody processes.
-        atomicOr(&ctl->err, DERR_CAPACITY);
-        if (s2 < c.segcap) segs_n[s2] = Seg{0u, 0u, seg.arr, 0u, 0u, 0u, 0u, 0u};
-      }
-      const uint32_t i = atomicAdd(&s_new_n, 1u);
-      s_new_owner[i] = ok ? s2 : NO_OWNER;
-      s_new_zero[i] = s2 < c.segcap ? s2 : NO_OWNER;
-      s_new_ts[i] = ts;
-      s_new_nt[i] = ts < c.tilecap ? min(nt, c.tilecap - ts) : 0u;
-      s_new_copy[i] = 0u;
-    }
-    if (cls == CLS_BIG_COPY) {
-      const uint32_t nt = (cnt + (uint32_t)TILE - 1) / (uint32_t)TILE;
-      const uint32_t q = atomicAdd(&ctl->copy_count, 1u);
-      const uint32_t ts = atomicAdd(&ctl->copy_tiles, nt);
-      const bool ok = q < c.copycap && ts + nt <= c.copytilecap;
-      if (ok)
-        c.copy_q[q] = CopyItem{off, cnt, seg.arr, ts, (unsigned long long)andv};
+    } else {
+      const uint32_t cnt = hist[(size_t)s * M + d];
+      const uint32_t excl = scan256(cnt, s_scan, nullptr);
+      if (threadIdx.x == 0) atomicAdd(&ctl->lv[L].keys, (unsigned long long)seg.len);
+      const uint32_t off = seg.off + excl;
+      const uint32_t pout = seg.parity ^ 1u;
+      uint32_t cls = CLS_NONE;
+      if (cnt == 0)
+        cls = CLS_NONE;
+      else if (cnt == 1 || (cnt > (uint32_t)TCTA && seg.shift == 0))
+        cls = !pout ? CLS_DONE : (cnt <= T_WARP ? CLS_TINY_COPY : CLS_BIG_COPY);
+      else if (cnt <= T_WARP)
+        cls = CLS_TINY_SORT;
+      else if (cnt <= (uint32_t)WCAP)
+        cls = CLS_WARP_SORT;
+      else if (cnt <= (uint32_t)TCTA)
+        cls = CLS_CTA_SORT;
       else
-        atomicOr(&ctl->err, DERR_CAPACITY);
-      const uint32_t i = atomicAdd(&s_new_n, 1u);
-      s_new_owner[i] = ok ? q : NO_OWNER;
-      s_new_zero[i] = NO_OWNER;
-      s_new_ts[i] = ts;
-      s_new_nt[i] = ts < c.copytilecap ? min(nt, c.copytilecap - ts) : 0u;
-      s_new_copy[i] = 1u;
-    }
-    // statistics
-    if (cls == CLS_DONE || cls == CLS_TINY_COPY || cls == CLS_CTA_COPY || cls == CLS_BIG_COPY) {
-      atomicAdd(&s_stat[0], 1ull);
-      atomicAdd(&s_stat[1], (unsigned long long)cnt);
-      if (cls != CLS_DONE) atomicAdd(&s_stat[2], (unsigned long long)cnt);
-    } else if (cls == CLS_TINY_SORT) {
-      atomicAdd(&s_stat[3], 1ull);
-      atomicAdd(&s_stat[4], (unsigned long long)cnt);
-    } else if (cls == CLS_CTA_SORT) {
-      atomicAdd(&s_stat[5], 1ull);
-      atomicAdd(&s_stat[6], (unsigned long long)cnt);
+        cls = CLS_BIG;
+
+      // Small and mid-size buckets: warp-aggregated appends to the warp-sort
+      // and CTA-sort queues.
+#pragma unroll
+      for (int qi = 0; qi < 2; ++qi) {
+        const bool want = cls == (qi ? CLS_CTA_SORT : CLS_WARP_SORT);
+        const uint32_t wm = __ballot_sync(FULL, want);
+        if (wm) {
+          const uint32_t first = (uint32_t)(__ffs(wm) - 1);
+          uint32_t qb = 0;
+          if (lane == first) qb = atomicAdd(qi ? &ctl->cta_count : &ctl->wq_count, (uint32_t)__popc(wm));
+          qb = __shfl_sync(FULL, qb, (int)first);
+          if (want) {
+            const uint32_t q = qb + (uint32_t)__popc(wm & lanemask_lt());
+            if (q < (qi ? c.ctacap : c.wqcap))
+              (qi ? c.cta_q : c.w_q)[q] = Item{off, cnt, seg.arr, pout};
+            else
+              atomicOr(&ctl->err, DERR_CAPACITY);
+          }
+        }
+      }
+      if (cls == CLS_TINY_SORT || cls == CLS_TINY_COPY) {
+        const uint32_t i = atomicAdd(&s_tiny_n, 1u);
+        s_tiny_off[i] = off;
+        s_tiny_len[i] = cnt | (cls == CLS_TINY_COPY ? 0x80000000u : 0u);
+      }
+      if (cls == CLS_BIG) {
+        // the bucket's varying bits all lie below the parent's window
+        const uint32_t b = window_bits<TCTA>(cnt, seg.shift, L + 1, c.nlev);
+        const uint32_t shift = seg.shift > b ? seg.shift - b : 0u;
+        add_big(off, cnt, seg.arr, shift, seg.shift - shift, pout, SEG_NEEDS_HIST | SEG_NEEDS_ANDOR, 0ull, 0ull);
+      }
+      if (cls == CLS_BIG_COPY) {
+        // all bits consumed: the bucket's keys are the segment prefix + digit
+        const K val = (K)(((K)seg.orv & ~(((K)(M - 1)) << seg.shift)) | ((K)d << seg.shift));
+        add_copy(off, cnt, seg.arr, (unsigned long long)val);
+      }
+      if (cls == CLS_DONE || cls == CLS_TINY_COPY || cls == CLS_BIG_COPY) {
+        atomicAdd(&s_stat[0], 1ull);
+        atomicAdd(&s_stat[1], (unsigned long long)cnt);
+        if (cls != CLS_DONE) atomicAdd(&s_stat[2], (unsigned long long)cnt);
+      } else if (cls == CLS_TINY_SORT) {
+        atomicAdd(&s_stat[3], 1ull);
+        atomicAdd(&s_stat[4], (unsigned long long)cnt);
+      } else if (cls == CLS_CTA_SORT) {
+        atomicAdd(&s_stat[5], 1ull);
+        atomicAdd(&s_stat[6], (unsigned long long)cnt);
+      } else if (cls == CLS_WARP_SORT) {
+        atomicAdd(&s_stat[7], (unsigned long long)cnt);
+        atomicAdd(&s_stat[8], 1ull);
+      }
     }
     __syncthreads();
 
-    // New segments: clear their histogram slots and fill the tile-owner map.
+    // New segments / copy items: clear histogram slots, fill tile-owner maps.
     const uint32_t nn = s_new_n;
     for (uint32_t i = 0; i < nn; ++i) {
       if (s_new_zero[i] != NO_OWNER) hist_n[(size_t)s_new_zero[i] * M + threadIdx.x] = 0u;
@@ -878,20 +1178,23 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
     }
     // Tiny buckets: one warp each.
     const uint32_t tn = s_tiny_n;
-    const ArrDesc ad = c.arrs[seg.arr];
-    const K* psrc = reinterpret_cast<const K*>(pout ? ad.buf : ad.keys);
-    const uint32_t* pvsrc = reinterpret_cast<const uint32_t*>(pout ? ad.vbuf : ad.vals);
-    for (uint32_t i = warp; i < tn; i += 8) {
-      const uint32_t o = s_tiny_off[i];
-      const uint32_t len = s_tiny_len[i] & 0x7fffffffu;
-      if (s_tiny_len[i] & 0x80000000u) {
-        if (lane < len) {
-          reinterpret_cast<K*>(ad.keys)[o + lane] = psrc[o + lane];
-          if constexpr (KV) reinterpret_cast<uint32_t*>(ad.vals)[o + lane] = pvsrc[o + lane];
+    if (tn) {
+      const ArrDesc ad = c.arrs[seg.arr];
+      const uint32_t pout = seg.parity ^ 1u;
+      const K* psrc = reinterpret_cast<const K*>(pout ? ad.buf : ad.keys);
+      const uint32_t* pvsrc = reinterpret_cast<const uint32_t*>(pout ? ad.vbuf : ad.vals);
+      for (uint32_t i = warp; i < tn; i += 8) {
+        const uint32_t o = s_tiny_off[i];
+        const uint32_t len = s_tiny_len[i] & 0x7fffffffu;
+        if (s_tiny_len[i] & 0x80000000u) {
+          if (lane < len) {
+            reinterpret_cast<K*>(ad.keys)[o + lane] = psrc[o + lane];
+            if constexpr (KV) reinterpret_cast<uint32_t*>(ad.vals)[o + lane] = pvsrc[o + lane];
+          }
+        } else {
+          warp_sort_tiny<K, KV>(psrc, pvsrc, reinterpret_cast<K*>(ad.keys), reinterpret_cast<uint32_t*>(ad.vals),
+                                o, len);
         }
-      } else {
-        warp_sort_tiny<K, KV>(psrc, pvsrc, reinterpret_cast<K*>(ad.keys), reinterpret_cast<uint32_t*>(ad.vals), o,
-                              len);
       }
     }
     if (threadIdx.x == 0) {
@@ -908,6 +1211,10 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
         atomicAdd(&ctl->cta_buckets, s_stat[5]);
         atomicAdd(&ctl->cta_keys, s_stat[6]);
       }
+      if (s_stat[7]) {
+        atomicAdd(&ctl->wsort_keys, s_stat[7]);
+        atomicAdd(&ctl->wsort_buckets, s_stat[8]);
+      }
     }
     __syncthreads();
   }
@@ -920,9 +1227,12 @@ constexpr size_t ctasort_smem_bytes() {
   return CAP * sizeof(K) + (KV ? CAP * 4 : 0) + (size_t)(NT / 32) * M * 4 + M * 4;
 }
 
-// Diversion sort of mid-size buckets: one CTA per bucket, a stable LSD radix
-// sort in shared memory over the bucket's varying bits only (windows of RB
-// bits, constant bits skipped), writing the final order into `keys`.
+// Diversion sort of mid-size buckets: one CTA per bucket, an LSD radix sort
+// in shared memory over the bucket's varying bits only (windows of RB bits,
+// constant bits skipped), writing the final order into `keys`.  Every pass
+// after the first is stable; the first is stable for key-value sorts (for key
+// only sorts the order before the first pass is irrelevant).  The number of
+// keys per thread follows the bucket size, so every warp has work.
 template <class K, class V, int NT, int KPT>
 __global__ void __launch_bounds__(NT, 2) k_ctasort(Ctx c) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
@@ -935,8 +1245,9 @@ __global__ void __launch_bounds__(NT, 2) k_ctasort(Ctx c) {
   uint32_t* s_whist = s_vals + (KV ? CAP : 0);
   uint32_t* s_dstart = s_whist + NW * M;
   __shared__ uint32_t s_scan[8];
+  __shared__ uint32_t s_scan16[NW];
   __shared__ uint32_t s_q;
-  __shared__ K s_or[NW], s_nand[NW];
+  __shared__ K s_red[2 * NW];
   Ctl* ctl = c.ctl;
   const uint32_t count = min(ctl->cta_count, c.ctacap);
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -963,8 +1274,9 @@ __global__ void __launch_bounds__(NT, 2) k_ctasort(Ctx c) {
       __syncthreads();
       continue;
     }
-    const uint32_t wb = warp * 32u * KPT;
-    const uint32_t wvalid = len > wb ? min(len - wb, 32u * KPT) : 0u;
+    const uint32_t kpt = (len + NT - 1) / NT;  // 1..KPT items per lane
+    const uint32_t wb = warp * 32u * kpt;
+    const uint32_t wvalid = len > wb ? min(len - wb, 32u * kpt) : 0u;
     K k[KPT];
     uint32_t r[KPT];
     uint32_t v[KV ? KPT : 1];
@@ -972,76 +1284,75 @@ __global__ void __launch_bounds__(NT, 2) k_ctasort(Ctx c) {
 #pragma unroll
     for (int i = 0; i < KPT; ++i) {
       const uint32_t e = (uint32_t)(i * 32) + lane;
-      if (e < wvalid) {
+      k[i] = K(0);
+      r[i] = 0u;
+      if ((uint32_t)i < kpt && e < wvalid) {
         k[i] = src[off + wb + e];
         if constexpr (KV) v[i] = vsrc[off + wb + e];
         orv |= k[i];
         nandv |= ~k[i];
-      } else {
-        k[i] = K(0);
       }
-      r[i] = 0u;
     }
-    orv = warp_or(orv);
-    nandv = warp_or(nandv);
-    if (lane == 0) {
-      s_or[warp] = orv;
-      s_nand[warp] = nandv;
-    }
-    __syncthreads();
-    K vm = 0;
-    {
-      K o = 0, na = 0;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        o |= s_or[w];
-        na |= s_nand[w];
-      }
-      vm = o & na;  // bits that are 1 in some key and 0 in another
-    }
+    block_or2<K, NT>(orv, nandv, s_red);
+    const K vm = orv & nandv;  // bits that are 1 in some key and 0 in another
     if (vm == K(0)) {
+      if (par) {
 #pragma unroll
-      for (int i = 0; i < KPT; ++i) {
-        const uint32_t e = (uint32_t)(i * 32) + lane;
-        if (e < wvalid) {
-          dst[off + wb + e] = k[i];
-          if constexpr (KV) vdst[off + wb + e] = v[i];
+        for (int i = 0; i < KPT; ++i) {
+          const uint32_t e = (uint32_t)(i * 32) + lane;
+          if ((uint32_t)i < kpt && e < wvalid) {
+            dst[off + wb + e] = k[i];
+            if constexpr (KV) vdst[off + wb + e] = v[i];
+          }
         }
       }
       __syncthreads();
       continue;
     }
     uint32_t sh = (uint32_t)low_bit<K>(vm);
+    bool first = true;
     for (;;) {
-      for (uint32_t i = threadIdx.x; i < (uint32_t)(NW * M); i += NT) s_whist[i] = 0u;
-      __syncthreads();
-      warp_rank<K, KPT>(k, sh, wvalid, wh, r);
-      __syncthreads();
-      uint32_t tcount = 0;
-      if (threadIdx.x < M) {
-        for (int w2 = 0; w2 < NW; ++w2) {
-          const uint32_t x = s_whist[w2 * M + threadIdx.x];
-          s_whist[w2 * M + threadIdx.x] = tcount;
-          tcount += x;
-        }
+      // Key-only first pass: block-wide counters, one returning atomic per
+      // key (order among equal digits is free before the first pass).
+      // Other passes: stable per-warp ranking, then one (digit, warp) scan.
+      const bool unstable = !KV && first;
+      if (unstable) {
+        if (threadIdx.x < M) s_dstart[threadIdx.x] = 0u;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < KPT; ++i)
+          if ((uint32_t)i < kpt)
+            r[i] = warp_inc<true>(s_dstart, digit_of(k[i], sh), (uint32_t)(i * 32) + lane < wvalid);
+        __syncthreads();
+        const uint32_t cnt = threadIdx.x < M ? s_dstart[threadIdx.x] : 0u;
+        const uint32_t ds = scan256(cnt, s_scan, nullptr);
+        if (threadIdx.x < M) s_dstart[threadIdx.x] = ds;
+      } else {
+        for (uint32_t i = threadIdx.x; i < (uint32_t)(NW * M); i += NT) s_whist[i] = 0u;
+        __syncthreads();
+        warp_rank_stable<K, KPT>(k, sh, 0u, wvalid, kpt, wh, r);
+        __syncthreads();
+        scan_digit_warp<NT, NW>(s_whist, s_scan16);
       }
-      const uint32_t ds = scan256(tcount, s_scan, nullptr);
-      if (threadIdx.x < M) s_dstart[threadIdx.x] = ds;
       __syncthreads();
 #pragma unroll
       for (int i = 0; i < KPT; ++i) {
-        if ((uint32_t)(i * 32) + lane < wvalid) {
+        if ((uint32_t)i < kpt) {
+          const bool valid = (uint32_t)(i * 32) + lane < wvalid;
           const uint32_t d = digit_of(k[i], sh);
-          const uint32_t pos = s_dstart[d] + wh[d] + r[i];
-          if (pos < len) {
-            s_keys[pos] = k[i];
-            if constexpr (KV) s_vals[pos] = v[i];
-          } else {
-            atomicOr(&ctl->err, DERR_BOUNDS);
+          const uint32_t pos = (unstable ? s_dstart[d] : wh[d]) + r[i];
+          if (valid) {
+            if (pos < len) {
+              s_keys[pos] = k[i];
+              if constexpr (KV) s_vals[pos] = v[i];
+            } else {
+              record_error(ctl, DERR_BOUNDS, ERR_SITE_CTASORT_STAGE);
+            }
           }
         }
       }
       __syncthreads();
+      first = false;
       const uint32_t nsh = sh + RB;
       const K rest = nsh < (uint32_t)W ? (K)(vm >> nsh) : K(0);
       if (rest == K(0)) break;
@@ -1049,7 +1360,7 @@ __global__ void __launch_bounds__(NT, 2) k_ctasort(Ctx c) {
 #pragma unroll
       for (int i = 0; i < KPT; ++i) {
         const uint32_t e = (uint32_t)(i * 32) + lane;
-        if (e < wvalid) {
+        if ((uint32_t)i < kpt && e < wvalid) {
           k[i] = s_keys[wb + e];
           if constexpr (KV) v[i] = s_vals[wb + e];
         }
@@ -1061,6 +1372,149 @@ __global__ void __launch_bounds__(NT, 2) k_ctasort(Ctx c) {
       if constexpr (KV) vdst[off + e] = s_vals[e];
     }
     __syncthreads();
+  }
+}
+
+template <class K, class V, int WKPT>
+constexpr size_t warpsort_warp_bytes() {
+  constexpr bool KV = !std::is_same<V, NoVal>::value;
+  constexpr size_t WCAP = (size_t)32 * WKPT;
+  return WCAP * sizeof(K) + (KV ? WCAP * 4 : 0) + M * 4;
+}
+
+// Diversion sort of small buckets (T_WARP < len <= 32 * WKPT): every warp
+// sorts its own buckets, pulled from the warp-sort queue, with an LSD radix
+// sort over the bucket's varying bits in its own slice of shared memory
+// (staging area + M counters) -- no block-wide barrier, so the many small
+// buckets of skewed inputs do not pay a whole CTA each.  Ranking as in
+// k_ctasort (stable except the first pass of a key-only sort).
+template <class K, class V, int WPB, int WKPT>
+__global__ void __launch_bounds__(WPB * 32) k_warpsort(Ctx c) {
+  constexpr bool KV = !std::is_same<V, NoVal>::value;
+  constexpr uint32_t WCAP = 32u * WKPT;
+  constexpr int W = 8 * sizeof(K);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  unsigned char* base = smem_raw + (size_t)warp * warpsort_warp_bytes<K, V, WKPT>();
+  K* sk = reinterpret_cast<K*>(base);
+  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + WCAP);
+  uint32_t* wh = sv + (KV ? WCAP : 0);
+  Ctl* ctl = c.ctl;
+  const uint32_t count = min(ctl->wq_count, c.wqcap);
+  for (;;) {
+    uint32_t q = 0;
+    if (lane == 0) q = atomicAdd(&ctl->wq_claim, 1u);
+    q = __shfl_sync(FULL, q, 0);
+    if (q >= count) break;
+    const Item it = c.w_q[q];
+    const ArrDesc ad = c.arrs[it.arr];
+    const bool par = (it.info & ITEM_PARITY) != 0u;
+    const K* src = reinterpret_cast<const K*>(par ? ad.buf : ad.keys);
+    const uint32_t* vsrc = reinterpret_cast<const uint32_t*>(par ? ad.vbuf : ad.vals);
+    K* dst = reinterpret_cast<K*>(ad.keys);
+    uint32_t* vdst = reinterpret_cast<uint32_t*>(ad.vals);
+    const uint32_t off = it.off, len = min(it.len, WCAP);
+    const uint32_t kpt = (len + 31u) / 32u;
+    K k[WKPT];
+    uint32_t r[WKPT];
+    uint32_t v[KV ? WKPT : 1];
+    K orv = 0, nandv = 0;
+#pragma unroll
+    for (int i = 0; i < WKPT; ++i) {
+      const uint32_t e = (uint32_t)(i * 32) + lane;
+      k[i] = K(0);
+      r[i] = 0u;
+      if ((uint32_t)i < kpt && e < len) {
+        k[i] = src[off + e];
+        if constexpr (KV) v[i] = vsrc[off + e];
+        orv |= k[i];
+        nandv |= ~k[i];
+      }
+    }
+    const K vm = warp_or(orv) & warp_or(nandv);
+    if (vm == K(0)) {
+      if (par) {
+#pragma unroll
+        for (int i = 0; i < WKPT; ++i) {
+          const uint32_t e = (uint32_t)(i * 32) + lane;
+          if ((uint32_t)i < kpt && e < len) {
+            dst[off + e] = k[i];
+            if constexpr (KV) vdst[off + e] = v[i];
+          }
+        }
+      }
+      continue;
+    }
+    uint32_t sh = (uint32_t)low_bit<K>(vm);
+    bool first = true;
+    for (;;) {
+#pragma unroll
+      for (int i = 0; i < M / 32; ++i) wh[i * 32 + lane] = 0u;
+      __syncwarp();
+      const bool unstable = !KV && first;
+      if (unstable) {
+#pragma unroll
+        for (int i = 0; i < WKPT; ++i)
+          if ((uint32_t)i < kpt) warp_inc<false>(wh, digit_of(k[i], sh), (uint32_t)(i * 32) + lane < len);
+      } else {
+        warp_rank_stable<K, WKPT>(k, sh, 0u, len, kpt, wh, r);
+      }
+      __syncwarp();
+      // exclusive scan of the M counters: lane l owns counters [l*8, l*8+8)
+      {
+        static_assert(M == 256, "the counter scan assumes 8 counters per lane");
+        uint4* w4 = reinterpret_cast<uint4*>(wh) + lane * 2;
+        const uint4 a = w4[0], b4 = w4[1];
+        const uint32_t x0 = 0, x1 = a.x, x2 = x1 + a.y, x3 = x2 + a.z, x4 = x3 + a.w, x5 = x4 + b4.x,
+                       x6 = x5 + b4.y, x7 = x6 + b4.z, run = x7 + b4.w;
+        uint32_t inc = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(FULL, inc, o);
+          if (lane >= (uint32_t)o) inc += y;
+        }
+        const uint32_t bv = inc - run;
+        w4[0] = make_uint4(bv + x0, bv + x1, bv + x2, bv + x3);
+        w4[1] = make_uint4(bv + x4, bv + x5, bv + x6, bv + x7);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < WKPT; ++i) {
+        if ((uint32_t)i < kpt) {
+          const bool valid = (uint32_t)(i * 32) + lane < len;
+          const uint32_t d = digit_of(k[i], sh);
+          const uint32_t pos = unstable ? warp_inc<true>(wh, d, valid) : wh[d] + r[i];
+          if (valid) {
+            if (pos < len) {
+              sk[pos] = k[i];
+              if constexpr (KV) sv[pos] = v[i];
+            } else {
+              record_error(ctl, DERR_BOUNDS, ERR_SITE_WARPSORT_STAGE);
+            }
+          }
+        }
+      }
+      __syncwarp();
+      first = false;
+      const uint32_t nsh = sh + RB;
+      const K rest = nsh < (uint32_t)W ? (K)(vm >> nsh) : K(0);
+      if (rest == K(0)) break;
+      sh = nsh + (uint32_t)low_bit<K>(rest);
+#pragma unroll
+      for (int i = 0; i < WKPT; ++i) {
+        const uint32_t e = (uint32_t)(i * 32) + lane;
+        if ((uint32_t)i < kpt && e < len) {
+          k[i] = sk[e];
+          if constexpr (KV) v[i] = sv[e];
+        }
+      }
+      __syncwarp();
+    }
+    for (uint32_t e = lane; e < len; e += 32) {
+      dst[off + e] = sk[e];
+      if constexpr (KV) vdst[off + e] = sv[e];
+    }
+    __syncwarp();
   }
 }
 

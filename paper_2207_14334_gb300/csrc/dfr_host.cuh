@@ -31,32 +31,33 @@ void rt_count_launch();
 int rt_grid(const void* kern, int threads, size_t smem);
 
 enum ProfKind { PK_INIT = 0, PK_ROOT_COUNT, PK_ROOT_CLASSIFY, PK_LEVEL_COUNT, PK_SCATTER, PK_CLASSIFY, PK_CTASORT,
-                PK_COPY, PK_H2D, PK_OTHER };
+                PK_COPY, PK_H2D, PK_WARPSORT };
 
-// Per key type: scatter tile (threads x keys per thread) and CTA-sort
-// capacity (threads x keys per thread) = the diversion threshold T_CTA.
+// Per key type: scatter tile (threads x keys per thread), CTA-sort capacity
+// (threads x keys per thread) = the diversion threshold T_CTA, and the warp
+// sort (warps per block, keys per lane; 32 x WKPT = its threshold).
 template <class K, class V>
 struct Cfg;
 template <>
 struct Cfg<uint32_t, NoVal> {
-  static constexpr int SNT = 512, SKPT = 16, CNT = 512, CKPT = 16;
+  static constexpr int SNT = 512, SKPT = 16, CNT = 512, CKPT = 16, WPB = 8, WKPT = 16;
 };
 template <>
 struct Cfg<uint32_t, uint32_t> {
-  static constexpr int SNT = 512, SKPT = 8, CNT = 512, CKPT = 8;
+  static constexpr int SNT = 512, SKPT = 8, CNT = 512, CKPT = 8, WPB = 8, WKPT = 16;
 };
 template <>
 struct Cfg<uint64_t, NoVal> {
-  static constexpr int SNT = 512, SKPT = 8, CNT = 512, CKPT = 8;
+  static constexpr int SNT = 512, SKPT = 8, CNT = 512, CKPT = 8, WPB = 8, WKPT = 16;
 };
 template <>
 struct Cfg<uint64_t, uint32_t> {
-  static constexpr int SNT = 512, SKPT = 8, CNT = 512, CKPT = 8;
+  static constexpr int SNT = 512, SKPT = 8, CNT = 512, CKPT = 8, WPB = 8, WKPT = 16;
 };
 
 struct Layout {
-  size_t ctl, arrs, root, segs0, segs1, hist0, hist1, a_nand, a_or, owner, status, ctaq, copyq, copyowner, total;
-  uint32_t segcap, tilecap, ctacap, copycap, copytilecap;
+  size_t ctl, arrs, root, segs0, segs1, hist0, hist1, owner, status, ctaq, wq, copyq, copyowner, total;
+  uint32_t segcap, tilecap, ctacap, wqcap, copycap, copytilecap;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -69,7 +70,9 @@ Layout make_layout(uint64_t ntot, uint32_t narr) {
   Layout l{};
   l.segcap = (uint32_t)(ntot / (TCTA + 1) + narr + 1);
   l.tilecap = (uint32_t)(ntot / TILE + l.segcap + 1);
-  l.ctacap = (uint32_t)(ntot / (T_WARP + 1) + narr + 1);
+  constexpr uint64_t WCAP = 32ull * C::WKPT;
+  l.ctacap = (uint32_t)(ntot / (WCAP + 1) + narr + 1);   // buckets of more than WCAP keys
+  l.wqcap = (uint32_t)(ntot / (T_WARP + 1) + narr + 1);  // buckets of more than T_WARP keys
   l.copycap = (uint32_t)(ntot / (TCTA + 1) + 1);
   l.copytilecap = (uint32_t)(ntot / TILE + l.copycap + 1);
   size_t o = 0;
@@ -87,16 +90,14 @@ Layout make_layout(uint64_t ntot, uint32_t narr) {
   o = align256(o + (size_t)l.segcap * M * 4);
   l.hist1 = o;
   o = align256(o + (size_t)l.segcap * M * 4);
-  l.a_nand = o;
-  o = align256(o + (size_t)l.segcap * M * sizeof(K));
-  l.a_or = o;
-  o = align256(o + (size_t)l.segcap * M * sizeof(K));
   l.owner = o;
   o = align256(o + (size_t)l.tilecap * 4);
   l.status = o;
   o = align256(o + (size_t)l.tilecap * M * 4);
   l.ctaq = o;
   o = align256(o + (size_t)l.ctacap * sizeof(Item));
+  l.wq = o;
+  o = align256(o + (size_t)l.wqcap * sizeof(Item));
   l.copyq = o;
   o = align256(o + (size_t)l.copycap * sizeof(CopyItem));
   l.copyowner = o;
@@ -116,16 +117,16 @@ inline Ctx make_ctx(void* ws, const Layout& l, uint32_t narr) {
   c.segs[1] = reinterpret_cast<Seg*>(b + l.segs1);
   c.hist[0] = reinterpret_cast<uint32_t*>(b + l.hist0);
   c.hist[1] = reinterpret_cast<uint32_t*>(b + l.hist1);
-  c.a_nand = b + l.a_nand;
-  c.a_or = b + l.a_or;
   c.tile_owner = reinterpret_cast<uint32_t*>(b + l.owner);
   c.status = reinterpret_cast<uint32_t*>(b + l.status);
   c.cta_q = reinterpret_cast<Item*>(b + l.ctaq);
+  c.w_q = reinterpret_cast<Item*>(b + l.wq);
   c.copy_q = reinterpret_cast<CopyItem*>(b + l.copyq);
   c.copy_owner = reinterpret_cast<uint32_t*>(b + l.copyowner);
   c.segcap = l.segcap;
   c.tilecap = l.tilecap;
   c.ctacap = l.ctacap;
+  c.wqcap = l.wqcap;
   c.copycap = l.copycap;
   c.copytilecap = l.copytilecap;
   return c;
@@ -168,22 +169,84 @@ size_t workspace_bytes(uint64_t ntot, uint32_t narr) {
   return make_layout<K, V>(ntot, narr).total;
 }
 
-template <class F>
-inline void launch(int kind, cudaStream_t st, F&& f) {
-  rt_prof_begin(kind, st);
-  f();
-  rt_count_launch();
-  rt_prof_end(kind, st);
+// Persistent grid sizes of every kernel of one key type on one device.
+struct Grids {
+  int rc, rcl, lc, sc, cl, cs, ws, cp;
+};
+
+template <class K, class V>
+struct Kernels {
+  using C = Cfg<K, V>;
+  static constexpr int SNT = C::SNT, SKPT = C::SKPT, TILE = SNT * SKPT;
+  static constexpr int CNT = C::CNT, CKPT = C::CKPT, TCTA = CNT * CKPT;
+  static constexpr int WPB = C::WPB, WKPT = C::WKPT, WCAP = 32 * WKPT;
+  static constexpr size_t sc_smem = scatter_smem_bytes<K, V, SNT, SKPT>();
+  static constexpr size_t cs_smem = ctasort_smem_bytes<K, V, CNT, CKPT>();
+  static constexpr size_t ws_smem = (size_t)WPB * warpsort_warp_bytes<K, V, WKPT>();
+  static constexpr int nlev = (int)sizeof(K) + EXTRA_LEVELS;
+  static_assert(nlev + 1 <= MAXLV, "control blocks for every launched level");
+  static constexpr auto root_count = k_root_count<K, SNT, TILE>;
+  static constexpr auto root_classify = k_root_classify<K, V, TILE, TCTA, WCAP>;
+  static constexpr auto level_count = k_level_count<K, SNT, TILE>;
+  static constexpr auto scatter = k_scatter<K, V, SNT, SKPT>;
+  static constexpr auto classify = k_classify<K, V, TILE, TCTA, WCAP>;
+  static constexpr auto ctasort = k_ctasort<K, V, CNT, CKPT>;
+  static constexpr auto warpsort = k_warpsort<K, V, WPB, WKPT>;
+  static constexpr auto copy = k_copy<K, V, SNT, TILE>;
+
+  // grid_of(kernel, threads, dynamic smem) -> persistent grid (or < 0 on error)
+  template <class G>
+  static bool grids(G&& grid_of, Grids* g) {
+    g->rc = grid_of((const void*)root_count, SNT, (size_t)0);
+    g->rcl = grid_of((const void*)root_classify, 256, (size_t)0);
+    g->lc = grid_of((const void*)level_count, SNT, (size_t)0);
+    g->sc = grid_of((const void*)scatter, SNT, sc_smem);
+    g->cl = grid_of((const void*)classify, 256, (size_t)0);
+    g->cs = grid_of((const void*)ctasort, CNT, cs_smem);
+    g->ws = grid_of((const void*)warpsort, WPB * 32, ws_smem);
+    g->cp = grid_of((const void*)copy, SNT, (size_t)0);
+    return g->rc > 0 && g->rcl > 0 && g->lc > 0 && g->sc > 0 && g->cl > 0 && g->cs > 0 && g->ws > 0 && g->cp > 0;
+  }
+};
+
+inline uint32_t min_u32(uint32_t a, uint32_t b) { return a < b ? a : b; }
+
+// The whole device launch sequence of one call (no host synchronisation, no
+// allocation).  `hook(kind, stream, launch_fn)` wraps every launch (profiling
+// and launch counting in the regular path, counting only in the no-allocation
+// path).  `a0` rides in k_init's parameters when `write_a0`.
+template <class K, class V, class Hook>
+void enqueue_sort(const Ctx& c, const Layout& lay, const Grids& g, uint32_t narr, uint32_t root_tiles,
+                  unsigned long long ntot, const ArrDesc& a0, bool write_a0, cudaStream_t st, Hook&& hook) {
+  using T = Kernels<K, V>;
+  const uint32_t root_words = (uint32_t)((size_t)narr * sizeof(RootAcc<K>) / 4);
+  const uint32_t words = (uint32_t)(sizeof(Ctl) / 4) + root_words;
+  const uint32_t gi = min_u32((words + 255) / 256, 1024u);
+  hook(PK_INIT, st, [&] { k_init<K><<<gi, 256, 0, st>>>(c, a0, write_a0 ? 1 : 0, root_words); });
+  hook(PK_ROOT_COUNT, st, [&] { T::root_count<<<min_u32(root_tiles, (uint32_t)g.rc), T::SNT, 0, st>>>(c, root_tiles); });
+  hook(PK_ROOT_CLASSIFY, st, [&] { T::root_classify<<<min_u32(narr, (uint32_t)g.rcl), 256, 0, st>>>(c, ntot); });
+  const uint32_t lc_grid = min_u32(lay.tilecap, (uint32_t)g.lc);
+  const uint32_t sc_grid = min_u32(lay.tilecap, (uint32_t)g.sc);
+  const uint32_t cl_grid = min_u32(lay.segcap, (uint32_t)g.cl);
+  for (int L = 0; L < T::nlev; ++L) {
+    hook(PK_LEVEL_COUNT, st, [&] { T::level_count<<<lc_grid, T::SNT, 0, st>>>(c, L); });
+    hook(PK_SCATTER, st, [&] { T::scatter<<<sc_grid, T::SNT, T::sc_smem, st>>>(c, L); });
+    hook(PK_CLASSIFY, st, [&] { T::classify<<<cl_grid, 256, 0, st>>>(c, L); });
+  }
+  hook(PK_CTASORT, st, [&] { T::ctasort<<<min_u32(lay.ctacap, (uint32_t)g.cs), T::CNT, T::cs_smem, st>>>(c); });
+  hook(PK_WARPSORT, st, [&] {
+    T::warpsort<<<min_u32((lay.wqcap + T::WPB - 1) / T::WPB, (uint32_t)g.ws), T::WPB * 32, T::ws_smem, st>>>(c);
+  });
+  hook(PK_COPY, st, [&] { T::copy<<<min_u32(lay.copytilecap, (uint32_t)g.cp), T::SNT, 0, st>>>(c); });
 }
 
-// Enqueue the whole sort of `narr` arrays.  `batch` = the descriptor table is
-// uploaded with one copy (else the single descriptor rides in k_init's
-// parameters, keeping the call a pure kernel sequence).
+// Regular entry: checks, layout, descriptor table, then enqueue_sort with
+// profiling hooks.  `batch` = the descriptor table is uploaded with one copy
+// (else the single descriptor rides in k_init's parameters, keeping the call
+// a pure kernel sequence).
 template <class K, class V>
 int run_sort(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws_bytes, cudaStream_t st) {
-  using C = Cfg<K, V>;
-  constexpr int SNT = C::SNT, SKPT = C::SKPT, TILE = SNT * SKPT;
-  constexpr int CNT = C::CNT, CKPT = C::CKPT, TCTA = CNT * CKPT;
+  using T = Kernels<K, V>;
   if (narr == 0) return DFR_OK;
   uint64_t ntot = 0;
   int rc = check_arrays<K, V>(arrs, narr, &ntot);
@@ -197,58 +260,32 @@ int run_sort(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws
   Ctx c = make_ctx(ws, lay, narr);
   c.spin_limit = rt_spin_limit();
   c.force_timeout = rt_force_timeout() ? 1u : 0u;
+  c.nlev = (uint32_t)T::nlev;
+
+  Grids g;
+  if (!T::grids([](const void* k, int t, size_t sm) { return rt_grid(k, t, sm); }, &g)) return DFR_ERR_CUDA;
 
   std::vector<ArrDesc> tab(narr);
   uint32_t rt = 0;
   for (uint32_t a = 0; a < narr; ++a) {
     const HostArr& h = arrs[a];
     tab[a] = ArrDesc{h.keys, h.buf, h.vals, h.vbuf, (uint32_t)h.n, rt};
-    if (h.n > 1) rt += (uint32_t)((h.n + TILE - 1) / TILE);
+    if (h.n > 1) rt += (uint32_t)((h.n + T::TILE - 1) / T::TILE);
   }
+  auto hook = [](int kind, cudaStream_t s, auto&& fn) {
+    rt_prof_begin(kind, s);
+    fn();
+    rt_count_launch();
+    rt_prof_end(kind, s);
+  };
   if (batch) {
     cudaError_t e = cudaSuccess;
-    launch(PK_H2D, st, [&] {
-      e = cudaMemcpyAsync(c.arrs, tab.data(), narr * sizeof(ArrDesc), cudaMemcpyHostToDevice, st);
-    });
+    rt_prof_begin(PK_H2D, st);
+    e = cudaMemcpyAsync(c.arrs, tab.data(), narr * sizeof(ArrDesc), cudaMemcpyHostToDevice, st);
+    rt_prof_end(PK_H2D, st);
     if (e != cudaSuccess) return DFR_ERR_CUDA;
   }
-  const uint32_t root_words = (uint32_t)((size_t)narr * sizeof(RootAcc<K>) / 4);
-  {
-    const uint32_t words = (uint32_t)(sizeof(Ctl) / 4) + root_words;
-    const uint32_t g = (words + 255) / 256 < 1024u ? (words + 255) / 256 : 1024u;
-    launch(PK_INIT, st, [&] { k_init<K><<<g, 256, 0, st>>>(c, tab[0], batch ? 0 : 1, root_words); });
-  }
-  auto kr = k_root_count<K, SNT, TILE>;
-  const int g_rc = rt_grid((const void*)kr, SNT, 0);
-  launch(PK_ROOT_COUNT, st, [&] { kr<<<rt < (uint32_t)g_rc ? rt : g_rc, SNT, 0, st>>>(c, rt); });
-  auto krc = k_root_classify<K, V, TILE, TCTA>;
-  const int g_rcl = rt_grid((const void*)krc, 256, 0);
-  launch(PK_ROOT_CLASSIFY, st, [&] { krc<<<narr < (uint32_t)g_rcl ? narr : g_rcl, 256, 0, st>>>(c, ntot); });
-
-  auto klc = k_level_count<K, SNT, TILE>;
-  auto ksc = k_scatter<K, V, SNT, SKPT>;
-  auto kcl = k_classify<K, V, TILE, TCTA>;
-  constexpr size_t sc_smem = scatter_smem_bytes<K, V, SNT, SKPT>();
-  const int g_lc = rt_grid((const void*)klc, SNT, 0);
-  const int g_sc = rt_grid((const void*)ksc, SNT, sc_smem);
-  const int g_cl = rt_grid((const void*)kcl, 256, 0);
-  const uint32_t lc_grid = lay.tilecap < (uint32_t)g_lc ? lay.tilecap : (uint32_t)g_lc;
-  const uint32_t sc_grid = lay.tilecap < (uint32_t)g_sc ? lay.tilecap : (uint32_t)g_sc;
-  const uint32_t cl_grid = lay.segcap < (uint32_t)g_cl ? lay.segcap : (uint32_t)g_cl;
-  for (int L = 0; L < (int)sizeof(K); ++L) {
-    launch(PK_LEVEL_COUNT, st, [&] { klc<<<lc_grid, SNT, 0, st>>>(c, L); });
-    launch(PK_SCATTER, st, [&] { ksc<<<sc_grid, SNT, sc_smem, st>>>(c, L); });
-    launch(PK_CLASSIFY, st, [&] { kcl<<<cl_grid, 256, 0, st>>>(c, L); });
-  }
-  auto kcs = k_ctasort<K, V, CNT, CKPT>;
-  constexpr size_t cs_smem = ctasort_smem_bytes<K, V, CNT, CKPT>();
-  const int g_cs = rt_grid((const void*)kcs, CNT, cs_smem);
-  const uint32_t cs_grid = lay.ctacap < (uint32_t)g_cs ? lay.ctacap : (uint32_t)g_cs;
-  launch(PK_CTASORT, st, [&] { kcs<<<cs_grid, CNT, cs_smem, st>>>(c); });
-  auto kcp = k_copy<K, V, SNT, TILE>;
-  const int g_cp = rt_grid((const void*)kcp, SNT, 0);
-  const uint32_t cp_grid = lay.copytilecap < (uint32_t)g_cp ? lay.copytilecap : (uint32_t)g_cp;
-  launch(PK_COPY, st, [&] { kcp<<<cp_grid, SNT, 0, st>>>(c); });
+  enqueue_sort<K, V>(c, lay, g, narr, rt, (unsigned long long)ntot, tab[0], !batch, st, hook);
   return cudaGetLastError() == cudaSuccess ? DFR_OK : DFR_ERR_CUDA;
 }
 

@@ -44,7 +44,7 @@ struct NoAllocDevice {
   bool ready;
   int status;
   unsigned char* base;  // device address of g_noalloc_scratch on this device
-  int g_rc, g_rcl, g_lc, g_sc, g_cl, g_cs, g_cp;
+  Grids grids;
 };
 
 constexpr int kMaxDevices = 64;
@@ -53,20 +53,7 @@ std::mutex g_noalloc_mu;
 
 using K = uint32_t;
 using V = NoVal;
-using C = Cfg<K, V>;
-constexpr int SNT = C::SNT, SKPT = C::SKPT, TILE = SNT * SKPT;
-constexpr int CNT = C::CNT, CKPT = C::CKPT, TCTA = CNT * CKPT;
-constexpr size_t kScatterSmem = scatter_smem_bytes<K, V, SNT, SKPT>();
-constexpr size_t kCtaSmem = ctasort_smem_bytes<K, V, CNT, CKPT>();
-
-int grid_of(const void* kern, int threads, size_t smem, int sms) {
-  int per_sm = 0;
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess) return -1;
-  return (per_sm < 1 ? 1 : per_sm) * sms;
-}
+using T = Kernels<K, V>;
 
 // Once per device, with the device current: resolve the scratch address and
 // the persistent grid sizes.  Returns a DFR status.
@@ -78,20 +65,18 @@ int setup(int dev, NoAllocDevice* d) {
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
     return DFR_ERR_CUDA;
-  d->g_rc = grid_of((const void*)k_root_count<K, SNT, TILE>, SNT, 0, sms);
-  d->g_rcl = grid_of((const void*)k_root_classify<K, V, TILE, TCTA>, 256, 0, sms);
-  d->g_lc = grid_of((const void*)k_level_count<K, SNT, TILE>, SNT, 0, sms);
-  d->g_sc = grid_of((const void*)k_scatter<K, V, SNT, SKPT>, SNT, kScatterSmem, sms);
-  d->g_cl = grid_of((const void*)k_classify<K, V, TILE, TCTA>, 256, 0, sms);
-  d->g_cs = grid_of((const void*)k_ctasort<K, V, CNT, CKPT>, CNT, kCtaSmem, sms);
-  d->g_cp = grid_of((const void*)k_copy<K, V, SNT, TILE>, SNT, 0, sms);
-  if (d->g_rc < 0 || d->g_rcl < 0 || d->g_lc < 0 || d->g_sc < 0 || d->g_cl < 0 || d->g_cs < 0 || d->g_cp < 0)
-    return DFR_ERR_CUDA;
+  auto grid_of = [sms](const void* kern, int threads, size_t smem) -> int {
+    int per_sm = 0;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess) return -1;
+    return (per_sm < 1 ? 1 : per_sm) * sms;
+  };
+  if (!T::grids(grid_of, &d->grids)) return DFR_ERR_CUDA;
   d->base = static_cast<unsigned char*>(p);
   return DFR_OK;
 }
-
-inline uint32_t min_u32(uint32_t a, uint32_t b) { return a < b ? a : b; }
 
 }  // namespace
 }  // namespace dfr
@@ -123,31 +108,13 @@ extern "C" int dfr_sort_u32_noalloc(uint32_t* keys, uint64_t n, dfr_stream_t str
   Ctx c = make_ctx(ws, lay, 1u);
   c.spin_limit = rt_spin_limit();
   c.force_timeout = 0u;
-
-  const uint32_t rt = (uint32_t)((n + TILE - 1) / TILE);
+  c.nlev = (uint32_t)T::nlev;
+  const uint32_t rt = (uint32_t)((n + T::TILE - 1) / T::TILE);
   const ArrDesc a0{keys, buf, nullptr, nullptr, (uint32_t)n, 0u};
-  const uint32_t root_words = (uint32_t)(sizeof(RootAcc<K>) / 4);
-  const uint32_t words = (uint32_t)(sizeof(Ctl) / 4) + root_words;
-  k_init<K><<<(words + 255) / 256, 256, 0, st>>>(c, a0, 1, root_words);
-  rt_count_launch();
-  k_root_count<K, SNT, TILE><<<min_u32(rt, (uint32_t)d->g_rc), SNT, 0, st>>>(c, rt);
-  rt_count_launch();
-  k_root_classify<K, V, TILE, TCTA><<<1, 256, 0, st>>>(c, (unsigned long long)n);
-  rt_count_launch();
-  const uint32_t lc_grid = min_u32(lay.tilecap, (uint32_t)d->g_lc);
-  const uint32_t sc_grid = min_u32(lay.tilecap, (uint32_t)d->g_sc);
-  const uint32_t cl_grid = min_u32(lay.segcap, (uint32_t)d->g_cl);
-  for (int L = 0; L < (int)sizeof(K); ++L) {
-    k_level_count<K, SNT, TILE><<<lc_grid, SNT, 0, st>>>(c, L);
-    rt_count_launch();
-    k_scatter<K, V, SNT, SKPT><<<sc_grid, SNT, kScatterSmem, st>>>(c, L);
-    rt_count_launch();
-    k_classify<K, V, TILE, TCTA><<<cl_grid, 256, 0, st>>>(c, L);
-    rt_count_launch();
-  }
-  k_ctasort<K, V, CNT, CKPT><<<min_u32(lay.ctacap, (uint32_t)d->g_cs), CNT, kCtaSmem, st>>>(c);
-  rt_count_launch();
-  k_copy<K, V, SNT, TILE><<<min_u32(lay.copytilecap, (uint32_t)d->g_cp), SNT, 0, st>>>(c);
-  rt_count_launch();
+  enqueue_sort<K, V>(c, lay, d->grids, 1u, rt, (unsigned long long)n, a0, true, st,
+                     [](int, cudaStream_t, auto&& fn) {
+                       fn();
+                       rt_count_launch();
+                     });
   return cudaGetLastError() == cudaSuccess ? DFR_OK : DFR_ERR_CUDA;
 }

@@ -14,7 +14,7 @@ from gpu_util import gpu_sort, need_gpu
 
 pytestmark = pytest.mark.gpu
 
-EDGE_SIZES = [0, 1, 2, 3, 31, 32, 33, 64, 100, 1000, 4095, 4096, 4097, 8191, 8192, 8193, 8194, 16385,
+EDGE_SIZES = [0, 1, 2, 3, 31, 32, 33, 64, 100, 511, 512, 513, 1000, 4095, 4096, 4097, 8191, 8192, 8193, 8194, 16385,
               65537, 300_001, 1_000_000, (1 << 21) + 12345]
 
 
@@ -119,9 +119,9 @@ def test_stats_uniform_plan(dfr):
     # 2^22 uniform keys: one level of 256 buckets of ~16K, a second level of
     # buckets of ~64 keys, which go to the CTA / warp diversion sorts
     assert st["level_keys"][0] == n
-    assert st["cta_keys"] + st["tiny_keys"] + st["const_keys"] == n
-    assert st["model_bytes"] == 4 * n + 8 * sum(st["level_keys"]) + 8 * (st["cta_keys"] + st["tiny_keys"]
-                                                                        + st["copy_keys"])
+    assert st["cta_keys"] + st["wsort_keys"] + st["tiny_keys"] + st["const_keys"] == n
+    assert st["model_bytes"] == 4 * n + 8 * sum(st["level_keys"]) + 8 * (st["cta_keys"] + st["wsort_keys"]
+                                                                        + st["tiny_keys"] + st["copy_keys"])
     torch.cuda.synchronize()
 
 
