@@ -367,7 +367,9 @@ def main():
                        "sort_roofline_frac": p["model_bytes"] / (t * 1e-3) / 1e9 / peak,
                        "levels": p["levels"], "level_keys": [k for k in p["level_keys"] if k],
                        "cta_keys": p["cta_keys"], "wsort_keys": p["wsort_keys"], "tiny_keys": p["tiny_keys"],
-                       "const_keys": p["const_keys"], "kernel_ms": prof_by_dist[d]}
+                       "const_keys": p["const_keys"], "group_buckets": p["group_buckets"],
+                       "cta_buckets": p["cta_buckets"], "wsort_buckets": p["wsort_buckets"],
+                       "kernel_ms": prof_by_dist[d]}
     kernel_share = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}
 
     # End to end through the C ABI: pinned host keys -> device -> sort -> host.

@@ -131,6 +131,8 @@ typedef struct {
     uint64_t wsort_buckets, wsort_keys;                /* diverted to the warp shared-memory sort */
     uint32_t device_error_site;                        /* first failed device check (0 = none; see dfr_api.cu) */
     uint32_t reserved;
+    uint64_t group_buckets;                            /* diverted key-only buckets finished by one counting pass
+                                                          plus in-group ranking */
 } dfr_stats_t;
 
 /* dfr_get_stats -- wait for `stream` and copy the counters of the last call

@@ -66,7 +66,8 @@ class dfr_stats_t(ctypes.Structure):
                 ("level_keys", _u64 * DFR_STATS_MAX_LEVELS), ("level_hist_keys", _u64 * DFR_STATS_MAX_LEVELS),
                 ("cta_buckets", _u64), ("cta_keys", _u64), ("tiny_buckets", _u64), ("tiny_keys", _u64),
                 ("const_buckets", _u64), ("const_keys", _u64), ("copy_keys", _u64), ("model_bytes", _u64),
-                ("wsort_buckets", _u64), ("wsort_keys", _u64), ("device_error_site", _u32), ("reserved", _u32)]
+                ("wsort_buckets", _u64), ("wsort_keys", _u64), ("device_error_site", _u32), ("reserved", _u32),
+                ("group_buckets", _u64)]
 
 
 _SIGNATURES = {

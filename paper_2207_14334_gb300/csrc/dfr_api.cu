@@ -191,6 +191,7 @@ int dfr_get_stats(const void* ws, dfr_stream_t stream, dfr_stats_t* out) {
   out->wsort_buckets = h.wsort_buckets;
   // 1 scatter staging, 2 scatter write, 3 CTA-sort staging, 4 warp-sort staging, 5 look-back timeout
   out->device_error_site = h.err_site;
+  out->group_buckets = h.group_buckets;
   out->wsort_keys = h.wsort_keys;
   return DFR_OK;
 }

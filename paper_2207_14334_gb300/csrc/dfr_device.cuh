@@ -136,6 +136,7 @@ struct Ctl {
   unsigned long long n_total;
   unsigned long long cta_buckets, cta_keys;
   unsigned long long wsort_buckets, wsort_keys;
+  unsigned long long group_buckets;  // diverted buckets finished by the key-only group pass
   unsigned long long tiny_buckets, tiny_keys;
   unsigned long long const_buckets, const_keys;
   unsigned long long copy_keys;
@@ -222,6 +223,12 @@ __device__ __forceinline__ K warp_or(K x) {
   return x;
 }
 
+__device__ __forceinline__ uint32_t warp_max(uint32_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(FULL, x, o));
+  return x;
+}
+
 __device__ __forceinline__ void atomic_or_u64(unsigned long long* p, unsigned long long v) { atomicOr(p, v); }
 
 // Record a failed device-side check: the error bit and, if it is the first,
@@ -256,10 +263,46 @@ __device__ __forceinline__ uint32_t scan256(uint32_t v, uint32_t* sh, uint32_t* 
   return pre + x - mine;
 }
 
-// Exclusive scan of one value per thread over the whole block of NT threads;
-// every thread must call it (it synchronises twice).  `sh` holds NT/32 words.
+// Two exclusive scans at once over threads [0, 256) (one synchronisation
+// pair instead of two); every thread of the block must call it.  `sh` holds
+// 16 words.
+__device__ __forceinline__ void scan256x2(uint32_t a, uint32_t b, uint32_t* sh, uint32_t& ea, uint32_t& eb) {
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+  const uint32_t ma = threadIdx.x < 256 ? a : 0u, mb = threadIdx.x < 256 ? b : 0u;
+  uint32_t x = ma, y = mb;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t xa = __shfl_up_sync(FULL, x, o);
+    const uint32_t yb = __shfl_up_sync(FULL, y, o);
+    if (lane >= (uint32_t)o) {
+      x += xa;
+      y += yb;
+    }
+  }
+  if (lane == 31 && w < 8) {
+    sh[w] = x;
+    sh[8 + w] = y;
+  }
+  __syncthreads();
+  uint32_t pa = 0, pb = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (i < (int)w) {
+      pa += sh[i];
+      pb += sh[8 + i];
+    }
+  }
+  __syncthreads();
+  ea = pa + x - ma;
+  eb = pb + y - mb;
+}
+
+// Exclusive scan of one value per thread over the whole block of NT threads
+// (NT <= 1024); every thread must call it (it synchronises twice).  `sh`
+// holds NT/32 words.  Warp totals are scanned by warp 0.
 template <int NT>
 __device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t* sh) {
+  constexpr int NW = NT / 32;
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
   uint32_t x = v;
 #pragma unroll
@@ -269,11 +312,18 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t* sh) {
   }
   if (lane == 31) sh[w] = x;
   __syncthreads();
-  uint32_t pre = 0;
+  if (w == 0) {
+    const uint32_t t = lane < (uint32_t)NW ? sh[lane] : 0u;
+    uint32_t u = t;
 #pragma unroll
-  for (int i = 0; i < NT / 32; ++i) pre += (i < (int)w) ? sh[i] : 0u;
+    for (int o = 1; o < NW; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, u, o);
+      if (lane >= (uint32_t)o) u += y;
+    }
+    if (lane < (uint32_t)NW) sh[lane] = u - t;
+  }
   __syncthreads();
-  return pre + x - v;
+  return sh[w] + x - v;
 }
 
 // Turn per-warp digit counts cnt[w][d] (NW x M words) into the shared-memory
@@ -769,7 +819,7 @@ __device__ __forceinline__ bool seg_is_dealt(const Seg& seg) {
 // Decoupled look-back for digit d of tile t (one thread per digit): sums the
 // counts of the earlier tiles of the segment back to the first inclusive
 // prefix, then publishes this tile's inclusive prefix.  Every wait is bounded
-// by c.spin_limit; a wait that runs out records DERR_TIMEOUT and *fail.
+// by c.spin_limit; a wait that runs out records DERR_TIMEOUT and sets *fail.
 __device__ __forceinline__ uint32_t look_back(const Ctx& c, uint32_t t, uint32_t tile_start, uint32_t d,
                                               uint32_t tcount, uint32_t* fail) {
   uint32_t* st = c.status + (size_t)t * M;
@@ -808,7 +858,9 @@ __device__ __forceinline__ uint32_t look_back(const Ctx& c, uint32_t t, uint32_t
 // single-pass decoupled look-back per digit, staged in digit order and
 // written to the other buffer, so each digit's run is contiguous in HBM.
 // Key-only: one returning shared atomic per key on block-wide counters gives
-// each key a distinct slot of its digit (order among equal digits is free);
+// each key a distinct slot of its digit (order among equal digits is free;
+// lanes hitting one counter are serialised by the hardware, which measured
+// cheaper than aggregating them in software even on skewed inputs);
 // full tiles of 16-byte-aligned arrays are read with 128-bit loads.
 // Key-value: stable per-warp ranking in element order.
 template <class K, class V, int NT, int KPT>
@@ -824,7 +876,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Ctx c, int L) {
   uint32_t* s_cnt = s_vals + (KV ? TILE : 0);  // KV: [NW][M] per warp; else [M]
   uint32_t* s_tstart = s_cnt + (KV ? NW * M : M);
   uint32_t* s_goff = s_tstart + M;  // global destination of staged element e of digit d = s_goff[d] + e
-  __shared__ uint32_t s_scan[8];
+  __shared__ uint32_t s_scan[16];
   __shared__ uint32_t s_t, s_fail;
 
   LevelCtl* lc = &c.ctl->lv[L];
@@ -914,7 +966,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Ctx c, int L) {
 #pragma unroll
       for (int i = 0; i < KPT; ++i) {
         const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
-        r[i] = warp_inc<true>(s_cnt, digit_of(k[i], shift), e >= vlo && e < vhi);
+        r[i] = (e >= vlo && e < vhi) ? atomicAdd(&s_cnt[digit_of(k[i], shift)], 1u) : 0u;
       }
     }
     __syncthreads();
@@ -933,9 +985,9 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Ctx c, int L) {
       }
       st_relaxed(c.status + (size_t)t * M + threadIdx.x, (j == 0 ? FLAG_INC : FLAG_AGG) | tcount);
     }
-    const uint32_t tstart = scan256(tcount, s_scan, nullptr);
     const uint32_t hcount = threadIdx.x < M ? hist[(size_t)s * M + threadIdx.x] : 0u;
-    const uint32_t bexcl = scan256(hcount, s_scan, nullptr);
+    uint32_t tstart, bexcl;
+    scan256x2(tcount, hcount, s_scan, tstart, bexcl);
     if (threadIdx.x < M) {
       const uint32_t excl = look_back(c, t, seg.tile_start, threadIdx.x, tcount, &s_fail);
       s_tstart[threadIdx.x] = tstart;
@@ -987,10 +1039,6 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Ctx c, int L) {
   }
 }
 
-enum : uint32_t {
-  CLS_NONE = 0, CLS_DONE, CLS_TINY_SORT, CLS_TINY_COPY, CLS_WARP_SORT, CLS_CTA_SORT, CLS_BIG, CLS_BIG_COPY
-};
-
 // Classification of one level, one CTA (256 threads = one per digit) per
 // segment.  A constant segment is finished (copied back if it sits in the
 // buffer); a segment whose window held no varying bit is passed to the next
@@ -1008,6 +1056,8 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
   // for their tile range, histogram slot to clear, first tile, tile count.
   __shared__ uint32_t s_new_owner[M], s_new_zero[M], s_new_ts[M], s_new_nt[M], s_new_copy[M];
   __shared__ unsigned long long s_stat[10];
+  __shared__ uint32_t s_bcnt[M], s_boff[M], s_run_off[M], s_run_len[M];
+  __shared__ uint32_t s_nrun, s_qn[2], s_qbase[2];
   Ctl* ctl = c.ctl;
   const uint32_t nseg = min(ctl->lv[L].nseg, c.segcap);
   const Seg* segs = ((L & 1) ? c.segs[1] : c.segs[0]);
@@ -1101,69 +1151,105 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
       if (threadIdx.x == 0) atomicAdd(&ctl->lv[L].keys, (unsigned long long)seg.len);
       const uint32_t off = seg.off + excl;
       const uint32_t pout = seg.parity ^ 1u;
-      uint32_t cls = CLS_NONE;
-      if (cnt == 0)
-        cls = CLS_NONE;
-      else if (cnt == 1 || (cnt > (uint32_t)TCTA && seg.shift == 0))
-        cls = !pout ? CLS_DONE : (cnt <= T_WARP ? CLS_TINY_COPY : CLS_BIG_COPY);
-      else if (cnt <= T_WARP)
-        cls = CLS_TINY_SORT;
-      else if (cnt <= (uint32_t)WCAP)
-        cls = CLS_WARP_SORT;
-      else if (cnt <= (uint32_t)TCTA)
-        cls = CLS_CTA_SORT;
-      else
-        cls = CLS_BIG;
-
-      // Small and mid-size buckets: warp-aggregated appends to the warp-sort
-      // and CTA-sort queues.
-#pragma unroll
-      for (int qi = 0; qi < 2; ++qi) {
-        const bool want = cls == (qi ? CLS_CTA_SORT : CLS_WARP_SORT);
-        const uint32_t wm = __ballot_sync(FULL, want);
-        if (wm) {
-          const uint32_t first = (uint32_t)(__ffs(wm) - 1);
-          uint32_t qb = 0;
-          if (lane == first) qb = atomicAdd(qi ? &ctl->cta_count : &ctl->wq_count, (uint32_t)__popc(wm));
-          qb = __shfl_sync(FULL, qb, (int)first);
-          if (want) {
-            const uint32_t q = qb + (uint32_t)__popc(wm & lanemask_lt());
-            if (q < (qi ? c.ctacap : c.wqcap))
-              (qi ? c.cta_q : c.w_q)[q] = Item{off, cnt, seg.arr, pout};
-            else
-              atomicOr(&ctl->err, DERR_CAPACITY);
+      // Large buckets go to the next level (or, when every bit is consumed,
+      // they are constant and only move back if they sit in the buffer).
+      if (cnt > (uint32_t)TCTA) {
+        if (seg.shift == 0u) {
+          atomicAdd(&s_stat[0], 1ull);
+          atomicAdd(&s_stat[1], (unsigned long long)cnt);
+          if (pout) {
+            atomicAdd(&s_stat[2], (unsigned long long)cnt);
+            // the bucket's keys are the segment prefix with this digit
+            const K val = (K)(((K)seg.orv & ~(((K)(M - 1)) << seg.shift)) | ((K)d << seg.shift));
+            add_copy(off, cnt, seg.arr, (unsigned long long)val);
           }
+        } else {
+          // the bucket's varying bits all lie below the parent's window
+          const uint32_t b = window_bits<TCTA>(cnt, seg.shift, L + 1, c.nlev);
+          const uint32_t shift = seg.shift > b ? seg.shift - b : 0u;
+          add_big(off, cnt, seg.arr, shift, seg.shift - shift, pout, SEG_NEEDS_HIST | SEG_NEEDS_ANDOR, 0ull, 0ull);
         }
       }
-      if (cls == CLS_TINY_SORT || cls == CLS_TINY_COPY) {
-        const uint32_t i = atomicAdd(&s_tiny_n, 1u);
-        s_tiny_off[i] = off;
-        s_tiny_len[i] = cnt | (cls == CLS_TINY_COPY ? 0x80000000u : 0u);
+      // Small buckets are diverted in bulk: consecutive ones (in digit order,
+      // hence adjacent in memory and ordered) are joined into runs of at
+      // most TCTA keys and each run is sorted as one item -- sorting the run
+      // sorts every bucket in it, and equal keys never span two buckets.
+      s_bcnt[d] = cnt > (uint32_t)TCTA ? 0xffffffffu : cnt;
+      s_boff[d] = off;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint32_t nr = 0, roff = 0, rlen = 0;
+        for (uint32_t x = 0; x < (uint32_t)M; ++x) {
+          const uint32_t cx = s_bcnt[x];
+          if (cx == 0u) continue;
+          if (cx == 0xffffffffu || rlen + cx > (uint32_t)TCTA) {
+            if (rlen) {
+              s_run_off[nr] = roff;
+              s_run_len[nr] = rlen;
+              ++nr;
+            }
+            rlen = 0;
+            if (cx == 0xffffffffu) continue;
+          }
+          if (rlen == 0) roff = s_boff[x];
+          rlen += cx;
+        }
+        if (rlen) {
+          s_run_off[nr] = roff;
+          s_run_len[nr] = rlen;
+          ++nr;
+        }
+        s_nrun = nr;
+        s_qn[0] = 0;
+        s_qn[1] = 0;
       }
-      if (cls == CLS_BIG) {
-        // the bucket's varying bits all lie below the parent's window
-        const uint32_t b = window_bits<TCTA>(cnt, seg.shift, L + 1, c.nlev);
-        const uint32_t shift = seg.shift > b ? seg.shift - b : 0u;
-        add_big(off, cnt, seg.arr, shift, seg.shift - shift, pout, SEG_NEEDS_HIST | SEG_NEEDS_ANDOR, 0ull, 0ull);
+      __syncthreads();
+      const uint32_t nr = s_nrun;
+      // run classes: single key, tiny (warp sort here), warp-sort queue, CTA queue
+      uint32_t rcls = 0, rloc = 0, rlen = 0, roff = 0;
+      if (threadIdx.x < nr) {
+        roff = s_run_off[threadIdx.x];
+        rlen = s_run_len[threadIdx.x];
+        if (rlen == 1u) {
+          atomicAdd(&s_stat[0], 1ull);
+          atomicAdd(&s_stat[1], 1ull);
+          if (pout) {
+            atomicAdd(&s_stat[2], 1ull);
+            rcls = 1;  // a single key in the buffer: copied by the tiny pass
+          }
+        } else if (rlen <= T_WARP) {
+          rcls = 2;
+          atomicAdd(&s_stat[3], 1ull);
+          atomicAdd(&s_stat[4], (unsigned long long)rlen);
+        } else if (rlen <= (uint32_t)WCAP) {
+          rcls = 3;
+          rloc = atomicAdd(&s_qn[0], 1u);
+          atomicAdd(&s_stat[8], 1ull);
+          atomicAdd(&s_stat[7], (unsigned long long)rlen);
+        } else {
+          rcls = 4;
+          rloc = atomicAdd(&s_qn[1], 1u);
+          atomicAdd(&s_stat[5], 1ull);
+          atomicAdd(&s_stat[6], (unsigned long long)rlen);
+        }
+        if (rcls == 1 || rcls == 2) {
+          const uint32_t i = atomicAdd(&s_tiny_n, 1u);
+          s_tiny_off[i] = roff;
+          s_tiny_len[i] = rlen | (rcls == 1 ? 0x80000000u : 0u);
+        }
       }
-      if (cls == CLS_BIG_COPY) {
-        // all bits consumed: the bucket's keys are the segment prefix + digit
-        const K val = (K)(((K)seg.orv & ~(((K)(M - 1)) << seg.shift)) | ((K)d << seg.shift));
-        add_copy(off, cnt, seg.arr, (unsigned long long)val);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s_qbase[0] = s_qn[0] ? atomicAdd(&ctl->wq_count, s_qn[0]) : 0u;
+        s_qbase[1] = s_qn[1] ? atomicAdd(&ctl->cta_count, s_qn[1]) : 0u;
       }
-      if (cls == CLS_DONE || cls == CLS_TINY_COPY || cls == CLS_BIG_COPY) {
-        atomicAdd(&s_stat[0], 1ull);
-        atomicAdd(&s_stat[1], (unsigned long long)cnt);
-        if (cls != CLS_DONE) atomicAdd(&s_stat[2], (unsigned long long)cnt);
-      } else if (cls == CLS_TINY_SORT) {
-        atomicAdd(&s_stat[3], 1ull);
-        atomicAdd(&s_stat[4], (unsigned long long)cnt);
-      } else if (cls == CLS_CTA_SORT) {
-        atomicAdd(&s_stat[5], 1ull);
-        atomicAdd(&s_stat[6], (unsigned long long)cnt);
-      } else if (cls == CLS_WARP_SORT) {
-        atomicAdd(&s_stat[7], (unsigned long long)cnt);
-        atomicAdd(&s_stat[8], 1ull);
+      __syncthreads();
+      if (rcls >= 3) {
+        const uint32_t q = s_qbase[rcls - 3] + rloc;
+        if (q < (rcls == 3 ? c.wqcap : c.ctacap))
+          (rcls == 3 ? c.w_q : c.cta_q)[q] = Item{roff, rlen, seg.arr, pout};
+        else
+          atomicOr(&ctl->err, DERR_CAPACITY);
       }
     }
     __syncthreads();
@@ -1220,6 +1306,19 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
   }
 }
 
+// Diversion sort of mid-size buckets: one CTA per bucket, writing the final
+// order into `keys`.  Every warp holds KPTA keys per lane (KPTA = the bucket
+// size over the block rounded up to a power of two, so the item loops are
+// fully unrolled).
+//  * Key-only buckets: one counting pass on the top (at most GB) varying bits
+//    groups the keys by those bits; if that covered every varying bit the
+//    groups hold equal keys and the bucket is sorted, otherwise each key is
+//    placed inside its (small) group by the rank an insertion sort would give
+//    it (keys below it, plus equal keys stored before it).  A group of more
+//    than GMAX keys (skewed bucket) falls back to the LSD passes.
+//  * Otherwise: an LSD radix sort in shared memory over the bucket's varying
+//    bits only (windows of RB bits, constant bits skipped); every pass is
+//    stable except the first of a key-only sort.
 template <class K, class V, int NT, int KPT>
 constexpr size_t ctasort_smem_bytes() {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
@@ -1227,18 +1326,192 @@ constexpr size_t ctasort_smem_bytes() {
   return CAP * sizeof(K) + (KV ? CAP * 4 : 0) + (size_t)(NT / 32) * M * 4 + M * 4;
 }
 
-// Diversion sort of mid-size buckets: one CTA per bucket, an LSD radix sort
-// in shared memory over the bucket's varying bits only (windows of RB bits,
-// constant bits skipped), writing the final order into `keys`.  Every pass
-// after the first is stable; the first is stable for key-value sorts (for key
-// only sorts the order before the first pass is irrelevant).  The number of
-// keys per thread follows the bucket size, so every warp has work.
+template <class K, class V, int NT, int KPT, int KPTA>
+__device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const uint32_t* vsrc, K* dst, uint32_t* vdst,
+                                                uint32_t off, uint32_t len, bool par, K* s_keys, uint32_t* s_vals,
+                                                uint32_t* s_whist, uint32_t* s_dstart, uint32_t* s_scan,
+                                                uint32_t* s_scan16, uint32_t* s_maxc,
+                                                unsigned long long* s_orv) {
+  constexpr bool KV = !std::is_same<V, NoVal>::value;
+  constexpr int NW = NT / 32;
+  constexpr int W = 8 * sizeof(K);
+  constexpr int GB = (NW * M >= 8192) ? 13 : (NW * M >= 4096) ? 12 : (NW * M >= 2048 ? 11 : 10);
+  constexpr uint32_t GMAX = 32;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  uint32_t* wh = s_whist + warp * M;
+  const uint32_t wb = warp * 32u * KPTA;
+  const uint32_t wvalid = len > wb ? min(len - wb, 32u * KPTA) : 0u;
+  K k[KPTA];
+  uint32_t r[KPTA];
+  uint32_t v[KV ? KPTA : 1];
+  K orv = 0, nandv = 0;
+#pragma unroll
+  for (int i = 0; i < KPTA; ++i) {
+    const uint32_t e = (uint32_t)(i * 32) + lane;
+    k[i] = K(0);
+    r[i] = 0u;
+    if (e < wvalid) {
+      k[i] = src[off + wb + e];
+      if constexpr (KV) v[i] = vsrc[off + wb + e];
+      orv |= k[i];
+      nandv |= ~k[i];
+    }
+  }
+  orv = warp_or(orv);
+  nandv = warp_or(nandv);
+  if (lane == 0) {
+    atomicOr(&s_orv[0], (unsigned long long)orv);
+    atomicOr(&s_orv[1], (unsigned long long)nandv);
+  }
+  __syncthreads();
+  const K vm = (K)s_orv[0] & (K)s_orv[1];  // bits that are 1 in some key and 0 in another
+  if (vm == K(0)) {
+    if (par) {
+#pragma unroll
+      for (int i = 0; i < KPTA; ++i) {
+        const uint32_t e = (uint32_t)(i * 32) + lane;
+        if (e < wvalid) {
+          dst[off + wb + e] = k[i];
+          if constexpr (KV) vdst[off + wb + e] = v[i];
+        }
+      }
+    }
+    return;
+  }
+  if constexpr (!KV) {
+    const int hb = top_bit<K>(vm), lb = low_bit<K>(vm);
+    const uint32_t span = (uint32_t)(hb - lb + 1);
+    const uint32_t wbits = span < (uint32_t)GB ? span : (uint32_t)GB;
+    const uint32_t gshift = (uint32_t)hb + 1u - wbits;
+    const uint32_t nb = 1u << wbits;
+    uint32_t* cnt = s_whist;  // nb <= NW * M counters
+    for (uint32_t x = threadIdx.x; x < nb; x += NT) cnt[x] = 0u;
+    if (threadIdx.x == 0) *s_maxc = 0u;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < KPTA; ++i)
+      r[i] = ((uint32_t)(i * 32) + lane < wvalid) ? atomicAdd(&cnt[(uint32_t)(k[i] >> gshift) & (nb - 1u)], 1u) : 0u;
+    __syncthreads();
+    {
+      // exclusive scan of the nb counters, EMAX consecutive ones per thread
+      constexpr uint32_t EMAX = (uint32_t)(NW * M) / NT;
+      const uint32_t e_per = nb >= (uint32_t)NT ? nb / NT : 1u;
+      const uint32_t first_c = threadIdx.x * e_per;
+      uint32_t tot = 0, mx = 0;
+#pragma unroll
+      for (uint32_t x = 0; x < EMAX; ++x) {
+        const uint32_t c0 = (x < e_per && first_c + x < nb) ? cnt[first_c + x] : 0u;
+        tot += c0;
+        mx = max(mx, c0);
+      }
+      mx = warp_max(mx);
+      if (lane == 0 && mx) atomicMax(s_maxc, mx);
+      uint32_t run = block_scan<NT>(tot, s_scan16);
+#pragma unroll
+      for (uint32_t x = 0; x < EMAX; ++x) {
+        if (x < e_per && first_c + x < nb) {
+          const uint32_t c0 = cnt[first_c + x];
+          cnt[first_c + x] = run;
+          run += c0;
+        }
+      }
+    }
+    __syncthreads();
+    if (span <= wbits || *s_maxc <= GMAX) {
+      if (threadIdx.x == 0) atomicAdd(&ctl->group_buckets, 1ull);
+#pragma unroll
+      for (int i = 0; i < KPTA; ++i) {
+        if ((uint32_t)(i * 32) + lane < wvalid) {
+          const uint32_t pos = cnt[(uint32_t)(k[i] >> gshift) & (nb - 1u)] + r[i];
+          if (pos < len)
+            s_keys[pos] = k[i];
+          else
+            record_error(ctl, DERR_BOUNDS, ERR_SITE_CTASORT_STAGE);
+        }
+      }
+      __syncthreads();
+      if (span <= wbits) {
+        for (uint32_t e = threadIdx.x; e < len; e += NT) dst[off + e] = s_keys[e];
+      } else {
+        for (uint32_t e = threadIdx.x; e < len; e += NT) {
+          const K key = s_keys[e];
+          const uint32_t h = (uint32_t)(key >> gshift) & (nb - 1u);
+          const uint32_t gs = cnt[h];
+          const uint32_t ge = h + 1u < nb ? cnt[h + 1u] : len;
+          uint32_t rank = 0;
+          for (uint32_t jj = gs; jj < ge; ++jj) {
+            const K kj = s_keys[jj];
+            rank += (kj < key || (kj == key && jj < e)) ? 1u : 0u;
+          }
+          dst[off + gs + rank] = key;
+        }
+      }
+      return;
+    }
+    // skewed bucket: LSD passes from the registers (r[] is recomputed)
+  }
+  uint32_t sh = (uint32_t)low_bit<K>(vm);
+  bool first = true;
+  for (;;) {
+    const bool unstable = !KV && first;
+    if (unstable) {
+      if (threadIdx.x < M) s_dstart[threadIdx.x] = 0u;
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < KPTA; ++i)
+        r[i] = warp_inc<true>(s_dstart, digit_of(k[i], sh), (uint32_t)(i * 32) + lane < wvalid);
+      __syncthreads();
+      const uint32_t cnt = threadIdx.x < M ? s_dstart[threadIdx.x] : 0u;
+      const uint32_t ds = scan256(cnt, s_scan, nullptr);
+      if (threadIdx.x < M) s_dstart[threadIdx.x] = ds;
+    } else {
+      for (uint32_t i = threadIdx.x; i < (uint32_t)(NW * M); i += NT) s_whist[i] = 0u;
+      __syncthreads();
+      warp_rank_stable<K, KPTA>(k, sh, 0u, wvalid, (uint32_t)KPTA, wh, r);
+      __syncthreads();
+      scan_digit_warp<NT, NW>(s_whist, s_scan16);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < KPTA; ++i) {
+      if ((uint32_t)(i * 32) + lane < wvalid) {
+        const uint32_t d = digit_of(k[i], sh);
+        const uint32_t pos = (unstable ? s_dstart[d] : wh[d]) + r[i];
+        if (pos < len) {
+          s_keys[pos] = k[i];
+          if constexpr (KV) s_vals[pos] = v[i];
+        } else {
+          record_error(ctl, DERR_BOUNDS, ERR_SITE_CTASORT_STAGE);
+        }
+      }
+    }
+    __syncthreads();
+    first = false;
+    const uint32_t nsh = sh + RB;
+    const K rest = nsh < (uint32_t)W ? (K)(vm >> nsh) : K(0);
+    if (rest == K(0)) break;
+    sh = nsh + (uint32_t)low_bit<K>(rest);
+#pragma unroll
+    for (int i = 0; i < KPTA; ++i) {
+      const uint32_t e = (uint32_t)(i * 32) + lane;
+      if (e < wvalid) {
+        k[i] = s_keys[wb + e];
+        if constexpr (KV) v[i] = s_vals[wb + e];
+      }
+    }
+    __syncthreads();
+  }
+  for (uint32_t e = threadIdx.x; e < len; e += NT) {
+    dst[off + e] = s_keys[e];
+    if constexpr (KV) vdst[off + e] = s_vals[e];
+  }
+}
+
 template <class K, class V, int NT, int KPT>
-__global__ void __launch_bounds__(NT, 2) k_ctasort(Ctx c) {
+__global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : 2)) k_ctasort(Ctx c) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr uint32_t CAP = (uint32_t)NT * KPT;
   constexpr int NW = NT / 32;
-  constexpr int W = 8 * sizeof(K);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   K* s_keys = reinterpret_cast<K*>(smem_raw);
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + CAP);
@@ -1246,15 +1519,17 @@ __global__ void __launch_bounds__(NT, 2) k_ctasort(Ctx c) {
   uint32_t* s_dstart = s_whist + NW * M;
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_scan16[NW];
-  __shared__ uint32_t s_q;
-  __shared__ K s_red[2 * NW];
+  __shared__ uint32_t s_q, s_maxc;
+  __shared__ unsigned long long s_orv[2];
   Ctl* ctl = c.ctl;
   const uint32_t count = min(ctl->cta_count, c.ctacap);
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  uint32_t* wh = s_whist + warp * M;
 
   for (;;) {
-    if (threadIdx.x == 0) s_q = atomicAdd(&ctl->cta_claim, 1u);
+    if (threadIdx.x == 0) {
+      s_q = atomicAdd(&ctl->cta_claim, 1u);
+      s_orv[0] = 0ull;
+      s_orv[1] = 0ull;
+    }
     __syncthreads();
     const uint32_t q = s_q;
     if (q >= count) break;
@@ -1271,108 +1546,48 @@ __global__ void __launch_bounds__(NT, 2) k_ctasort(Ctx c) {
         dst[off + e] = src[off + e];
         if constexpr (KV) vdst[off + e] = vsrc[off + e];
       }
-      __syncthreads();
-      continue;
-    }
-    const uint32_t kpt = (len + NT - 1) / NT;  // 1..KPT items per lane
-    const uint32_t wb = warp * 32u * kpt;
-    const uint32_t wvalid = len > wb ? min(len - wb, 32u * kpt) : 0u;
-    K k[KPT];
-    uint32_t r[KPT];
-    uint32_t v[KV ? KPT : 1];
-    K orv = 0, nandv = 0;
-#pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-      const uint32_t e = (uint32_t)(i * 32) + lane;
-      k[i] = K(0);
-      r[i] = 0u;
-      if ((uint32_t)i < kpt && e < wvalid) {
-        k[i] = src[off + wb + e];
-        if constexpr (KV) v[i] = vsrc[off + wb + e];
-        orv |= k[i];
-        nandv |= ~k[i];
-      }
-    }
-    block_or2<K, NT>(orv, nandv, s_red);
-    const K vm = orv & nandv;  // bits that are 1 in some key and 0 in another
-    if (vm == K(0)) {
-      if (par) {
-#pragma unroll
-        for (int i = 0; i < KPT; ++i) {
-          const uint32_t e = (uint32_t)(i * 32) + lane;
-          if ((uint32_t)i < kpt && e < wvalid) {
-            dst[off + wb + e] = k[i];
-            if constexpr (KV) vdst[off + wb + e] = v[i];
-          }
-        }
-      }
-      __syncthreads();
-      continue;
-    }
-    uint32_t sh = (uint32_t)low_bit<K>(vm);
-    bool first = true;
-    for (;;) {
-      // Key-only first pass: block-wide counters, one returning atomic per
-      // key (order among equal digits is free before the first pass).
-      // Other passes: stable per-warp ranking, then one (digit, warp) scan.
-      const bool unstable = !KV && first;
-      if (unstable) {
-        if (threadIdx.x < M) s_dstart[threadIdx.x] = 0u;
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < KPT; ++i)
-          if ((uint32_t)i < kpt)
-            r[i] = warp_inc<true>(s_dstart, digit_of(k[i], sh), (uint32_t)(i * 32) + lane < wvalid);
-        __syncthreads();
-        const uint32_t cnt = threadIdx.x < M ? s_dstart[threadIdx.x] : 0u;
-        const uint32_t ds = scan256(cnt, s_scan, nullptr);
-        if (threadIdx.x < M) s_dstart[threadIdx.x] = ds;
-      } else {
-        for (uint32_t i = threadIdx.x; i < (uint32_t)(NW * M); i += NT) s_whist[i] = 0u;
-        __syncthreads();
-        warp_rank_stable<K, KPT>(k, sh, 0u, wvalid, kpt, wh, r);
-        __syncthreads();
-        scan_digit_warp<NT, NW>(s_whist, s_scan16);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < KPT; ++i) {
-        if ((uint32_t)i < kpt) {
-          const bool valid = (uint32_t)(i * 32) + lane < wvalid;
-          const uint32_t d = digit_of(k[i], sh);
-          const uint32_t pos = (unstable ? s_dstart[d] : wh[d]) + r[i];
-          if (valid) {
-            if (pos < len) {
-              s_keys[pos] = k[i];
-              if constexpr (KV) s_vals[pos] = v[i];
-            } else {
-              record_error(ctl, DERR_BOUNDS, ERR_SITE_CTASORT_STAGE);
-            }
-          }
-        }
-      }
-      __syncthreads();
-      first = false;
-      const uint32_t nsh = sh + RB;
-      const K rest = nsh < (uint32_t)W ? (K)(vm >> nsh) : K(0);
-      if (rest == K(0)) break;
-      sh = nsh + (uint32_t)low_bit<K>(rest);
-#pragma unroll
-      for (int i = 0; i < KPT; ++i) {
-        const uint32_t e = (uint32_t)(i * 32) + lane;
-        if ((uint32_t)i < kpt && e < wvalid) {
-          k[i] = s_keys[wb + e];
-          if constexpr (KV) v[i] = s_vals[wb + e];
-        }
-      }
-      __syncthreads();
-    }
-    for (uint32_t e = threadIdx.x; e < len; e += NT) {
-      dst[off + e] = s_keys[e];
-      if constexpr (KV) vdst[off + e] = s_vals[e];
+    } else {
+      const uint32_t kpt = (len + NT - 1) / NT;  // 1..KPT keys per lane
+#define DFR_CTA_BODY(A)                                                                                      \
+  cta_sort_bucket<K, V, NT, KPT, A>(ctl, src, vsrc, dst, vdst, off, len, par, s_keys, s_vals, s_whist, s_dstart, \
+                                    s_scan, s_scan16, &s_maxc, s_orv)
+      if (kpt <= 1)
+        DFR_CTA_BODY(1);
+      else if (kpt <= 2)
+        DFR_CTA_BODY(KPT >= 2 ? 2 : KPT);
+      else if (kpt <= 4)
+        DFR_CTA_BODY(KPT >= 4 ? 4 : KPT);
+      else if (kpt <= 8)
+        DFR_CTA_BODY(KPT >= 8 ? 8 : KPT);
+      else
+        DFR_CTA_BODY(KPT);
+#undef DFR_CTA_BODY
     }
     __syncthreads();
   }
+}
+
+// Exclusive scan, in place, of a warp's M = 256 counters (lane l owns
+// counters 8l..8l+7); returns the largest counter.  Call with the whole warp.
+__device__ __forceinline__ uint32_t warp_scan_counters(uint32_t* wh) {
+  static_assert(M == 256, "the counter scan assumes 8 counters per lane");
+  const uint32_t lane = lane_id();
+  uint4* w4 = reinterpret_cast<uint4*>(wh) + lane * 2;
+  const uint4 a = w4[0], b4 = w4[1];
+  const uint32_t x0 = 0, x1 = a.x, x2 = x1 + a.y, x3 = x2 + a.z, x4 = x3 + a.w, x5 = x4 + b4.x, x6 = x5 + b4.y,
+                 x7 = x6 + b4.z, run = x7 + b4.w;
+  uint32_t mx = max(max(max(a.x, a.y), max(a.z, a.w)), max(max(b4.x, b4.y), max(b4.z, b4.w)));
+  uint32_t inc = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, inc, o);
+    if (lane >= (uint32_t)o) inc += y;
+    mx = max(mx, __shfl_xor_sync(FULL, mx, o));
+  }
+  const uint32_t bv = inc - run;
+  w4[0] = make_uint4(bv + x0, bv + x1, bv + x2, bv + x3);
+  w4[1] = make_uint4(bv + x4, bv + x5, bv + x6, bv + x7);
+  return mx;
 }
 
 template <class K, class V, int WKPT>
@@ -1445,6 +1660,57 @@ __global__ void __launch_bounds__(WPB * 32) k_warpsort(Ctx c) {
       }
       continue;
     }
+    if constexpr (!KV) {
+      // Key-only: count on the top (at most RB) varying bits, then the
+      // insertion-sort rank inside each small group (as in k_ctasort); a group
+      // of more than GMAX keys falls back to the LSD passes below.
+      constexpr uint32_t GMAX = 32;
+      const int hb = top_bit<K>(vm), lb = low_bit<K>(vm);
+      const uint32_t span = (uint32_t)(hb - lb + 1);
+      const uint32_t wbits = span < (uint32_t)RB ? span : (uint32_t)RB;
+      const uint32_t gshift = (uint32_t)hb + 1u - wbits;
+#pragma unroll
+      for (int i = 0; i < M / 32; ++i) wh[i * 32 + lane] = 0u;
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < WKPT; ++i)
+        if ((uint32_t)i < kpt) r[i] = warp_inc<true>(wh, digit_of(k[i], gshift), (uint32_t)(i * 32) + lane < len);
+      __syncwarp();
+      const uint32_t maxc = warp_scan_counters(wh);
+      __syncwarp();
+      if (span <= wbits || maxc <= GMAX) {
+        if (lane == 0) atomicAdd(&ctl->group_buckets, 1ull);
+#pragma unroll
+        for (int i = 0; i < WKPT; ++i) {
+          if ((uint32_t)i < kpt && (uint32_t)(i * 32) + lane < len) {
+            const uint32_t pos = wh[digit_of(k[i], gshift)] + r[i];
+            if (pos < len)
+              sk[pos] = k[i];
+            else
+              record_error(ctl, DERR_BOUNDS, ERR_SITE_WARPSORT_STAGE);
+          }
+        }
+        __syncwarp();
+        if (span <= wbits) {
+          for (uint32_t e = lane; e < len; e += 32) dst[off + e] = sk[e];
+        } else {
+          for (uint32_t e = lane; e < len; e += 32) {
+            const K key = sk[e];
+            const uint32_t h = digit_of(key, gshift);  // the same 8-bit index the counters used
+            const uint32_t gs = wh[h];
+            const uint32_t ge = h + 1u < (uint32_t)M ? wh[h + 1u] : len;
+            uint32_t rank = 0;
+            for (uint32_t jj = gs; jj < ge; ++jj) {
+              const K kj = sk[jj];
+              rank += (kj < key || (kj == key && jj < e)) ? 1u : 0u;
+            }
+            dst[off + gs + rank] = key;
+          }
+        }
+        __syncwarp();
+        continue;
+      }
+    }
     uint32_t sh = (uint32_t)low_bit<K>(vm);
     bool first = true;
     for (;;) {
@@ -1460,23 +1726,7 @@ __global__ void __launch_bounds__(WPB * 32) k_warpsort(Ctx c) {
         warp_rank_stable<K, WKPT>(k, sh, 0u, len, kpt, wh, r);
       }
       __syncwarp();
-      // exclusive scan of the M counters: lane l owns counters [l*8, l*8+8)
-      {
-        static_assert(M == 256, "the counter scan assumes 8 counters per lane");
-        uint4* w4 = reinterpret_cast<uint4*>(wh) + lane * 2;
-        const uint4 a = w4[0], b4 = w4[1];
-        const uint32_t x0 = 0, x1 = a.x, x2 = x1 + a.y, x3 = x2 + a.z, x4 = x3 + a.w, x5 = x4 + b4.x,
-                       x6 = x5 + b4.y, x7 = x6 + b4.z, run = x7 + b4.w;
-        uint32_t inc = run;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(FULL, inc, o);
-          if (lane >= (uint32_t)o) inc += y;
-        }
-        const uint32_t bv = inc - run;
-        w4[0] = make_uint4(bv + x0, bv + x1, bv + x2, bv + x3);
-        w4[1] = make_uint4(bv + x4, bv + x5, bv + x6, bv + x7);
-      }
+      warp_scan_counters(wh);
       __syncwarp();
 #pragma unroll
       for (int i = 0; i < WKPT; ++i) {
