@@ -197,6 +197,60 @@ int dfr_batch_workspace_bytes(const dfr_segment_t* segs, uint32_t count, size_t*
 int dfr_sort_batch(const dfr_segment_t* segs, uint32_t count, void* ws, size_t ws_bytes,
                    dfr_stream_t stream);
 
+/* --------------------------------------------------------------- served -- */
+
+/*
+ * The served form: a stream of independent sort requests under a device
+ * memory budget.  The paper sorts one array at a time and has no such loop;
+ * this is the standard request-batching pattern of a serving system put over
+ * dfr_sort_batch.  A server owns one device pool of the budget's size and a
+ * dispatcher thread.  Requests are admitted in arrival order; the oldest
+ * pending request and the later ones of its key type are coalesced into one
+ * batched launch sequence while their workspace and scratch fit the pool's
+ * largest free block; up to `n_streams` batches run at once, each on its own
+ * stream.  A request's result is exactly that of sorting its array alone.
+ *
+ * Ownership: the caller's `keys` / `vals` (and optional `kbuf` / `vbuf`)
+ * device buffers must stay valid and untouched from dfr_submit until the
+ * request is done.  Requests with NULL `kbuf` / `vbuf` get scratch from the
+ * pool.  The caller orders its own writes of the inputs before dfr_submit
+ * (e.g. cudaStreamSynchronize on the producing stream); the server's streams
+ * do not wait on any caller stream.
+ */
+typedef struct dfr_server dfr_server_t;
+#define DFR_SERVER_MAX_STREAMS 64
+
+/* dfr_server_create -- a server on `device` owning `mem_budget_bytes` of
+ * device memory (allocated here, >= 4096) with `n_streams` streams (1 ..
+ * DFR_SERVER_MAX_STREAMS).  DFR_ERR_CUDA if an allocation fails. */
+int dfr_server_create(dfr_server_t** server, int device, size_t mem_budget_bytes, int n_streams);
+
+/* dfr_submit -- queue one request (`req` is copied) and return its ticket.
+ * Errors (nothing queued): DFR_ERR_INVALID_ARG for an unknown key type,
+ * n > DFR_MAX_N, a null or misaligned buffer; DFR_ERR_OVER_BUDGET when the
+ * request's workspace plus its server-provided scratch alone exceed the
+ * budget; DFR_ERR_BUSY once the server is being destroyed. */
+int dfr_submit(dfr_server_t* server, const dfr_segment_t* req, uint64_t* ticket);
+
+/* dfr_poll -- *done = 1 once the request's sort has completed on the device;
+ * then *latency_us (may be NULL) = completion time - submission time in
+ * microseconds, the ticket is released and the request's status is returned
+ * (DFR_OK, or a device error: DFR_ERR_TIMEOUT, DFR_ERR_BOUNDS,
+ * DFR_ERR_WORKSPACE).  While pending: *done = 0 and DFR_OK.  An unknown or
+ * released ticket gives DFR_ERR_INVALID_ARG. */
+int dfr_poll(dfr_server_t* server, uint64_t ticket, int* done, double* latency_us);
+
+/* dfr_wait -- block until the request is done; then as dfr_poll. */
+int dfr_wait(dfr_server_t* server, uint64_t ticket, double* latency_us);
+
+/* dfr_server_stats -- batches launched so far, requests pending and batches
+ * in flight (each pointer may be NULL). */
+int dfr_server_stats(dfr_server_t* server, uint64_t* batches, uint64_t* pending, uint64_t* inflight);
+
+/* dfr_server_destroy -- finish every queued request, then free the pool, the
+ * streams and the server.  Tickets not yet polled are released. */
+int dfr_server_destroy(dfr_server_t* server);
+
 /* ---------------------------------------------------- debug and profiling -- */
 
 /*

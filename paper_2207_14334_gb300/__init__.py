@@ -37,6 +37,7 @@ DFR_MAX_N = (1 << 30) - 1
 DFR_NOALLOC_MAX_N = 1 << 20
 DFR_PROFILE_KINDS = 10
 DFR_STATS_MAX_LEVELS = 16
+DFR_SERVER_MAX_STREAMS = 64
 
 KEY_BYTES = {DFR_U32: 4, DFR_U64: 8, DFR_U64_KV: 8, DFR_U32_KV: 4}
 HAS_VALS = {DFR_U32: False, DFR_U64: False, DFR_U64_KV: True, DFR_U32_KV: True}
@@ -81,6 +82,12 @@ _SIGNATURES = {
     "dfr_get_stats": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(dfr_stats_t)]),
     "dfr_batch_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(dfr_segment_t), _u32, ctypes.POINTER(_sz)]),
     "dfr_sort_batch": (ctypes.c_int, [ctypes.POINTER(dfr_segment_t), _u32, _vp, _sz, _vp]),
+    "dfr_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _sz, ctypes.c_int]),
+    "dfr_submit": (ctypes.c_int, [_vp, ctypes.POINTER(dfr_segment_t), ctypes.POINTER(_u64)]),
+    "dfr_poll": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "dfr_wait": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(ctypes.c_double)]),
+    "dfr_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "dfr_server_destroy": (ctypes.c_int, [_vp]),
     "dfr_set_debug": (ctypes.c_int, [_u32, ctypes.c_int]),
     "dfr_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "dfr_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64)]),
@@ -215,6 +222,49 @@ def dfr_batch_workspace_bytes(segs) -> int:
 def dfr_sort_batch(segs, ws, ws_bytes, stream=None) -> int:
     arr = _segments(segs)
     return load().dfr_sort_batch(arr, len(segs), _ptr(ws), int(ws_bytes), _stream(stream))
+
+
+def dfr_server_create(device: int, mem_budget_bytes: int, n_streams: int) -> int:
+    """Returns the server handle (an int); raises DfrError on failure."""
+    h = _vp(0)
+    check(load().dfr_server_create(ctypes.byref(h), int(device), int(mem_budget_bytes), int(n_streams)),
+          "dfr_server_create")
+    return int(h.value)
+
+
+def dfr_submit(server: int, seg) -> tuple:
+    """Queue one request (a segment dict or tuple, as for dfr_sort_batch).
+    Returns (status, ticket); the ticket is meaningful only for DFR_OK."""
+    arr = _segments([seg])
+    t = _u64(0)
+    rc = load().dfr_submit(_vp(server), arr, ctypes.byref(t))
+    return int(rc), int(t.value)
+
+
+def dfr_poll(server: int, ticket: int) -> tuple:
+    """Returns (status, done, latency_us)."""
+    d = ctypes.c_int(0)
+    lat = ctypes.c_double(0.0)
+    rc = load().dfr_poll(_vp(server), int(ticket), ctypes.byref(d), ctypes.byref(lat))
+    return int(rc), bool(d.value), float(lat.value)
+
+
+def dfr_wait(server: int, ticket: int) -> tuple:
+    """Returns (status, latency_us)."""
+    lat = ctypes.c_double(0.0)
+    rc = load().dfr_wait(_vp(server), int(ticket), ctypes.byref(lat))
+    return int(rc), float(lat.value)
+
+
+def dfr_server_stats(server: int) -> dict:
+    b, p, f = _u64(0), _u64(0), _u64(0)
+    check(load().dfr_server_stats(_vp(server), ctypes.byref(b), ctypes.byref(p), ctypes.byref(f)),
+          "dfr_server_stats")
+    return {"batches": int(b.value), "pending": int(p.value), "inflight": int(f.value)}
+
+
+def dfr_server_destroy(server: int) -> int:
+    return load().dfr_server_destroy(_vp(server))
 
 
 def dfr_set_debug(spin_limit: int = 0, force_timeout: bool = False) -> int:

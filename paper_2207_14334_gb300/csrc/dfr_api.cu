@@ -80,15 +80,14 @@ int rt_grid(const void* kern, int threads, size_t smem) {
   return grid;
 }
 
-static int map_device_status(uint32_t err) {
+int map_device_status(uint32_t err) {
   if (err & DERR_TIMEOUT) return DFR_ERR_TIMEOUT;
   if (err & DERR_BOUNDS) return DFR_ERR_BOUNDS;
   if (err & DERR_CAPACITY) return DFR_ERR_WORKSPACE;
   return DFR_OK;
 }
 
-static int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb,
-                     cudaStream_t st) {
+int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st) {
   switch (key_type) {
     case DFR_U32: return run_u32(a, n, batch, ws, wsb, st);
     case DFR_U32_KV: return run_u32_kv(a, n, batch, ws, wsb, st);
@@ -98,7 +97,7 @@ static int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, voi
   }
 }
 
-static int ws_typed(int key_type, uint64_t ntot, uint32_t narr, size_t* bytes) {
+int ws_typed(int key_type, uint64_t ntot, uint32_t narr, size_t* bytes) {
   switch (key_type) {
     case DFR_U32: *bytes = ws_u32(ntot, narr); return DFR_OK;
     case DFR_U32_KV: *bytes = ws_u32_kv(ntot, narr); return DFR_OK;

@@ -298,5 +298,9 @@ size_t ws_u32(uint64_t ntot, uint32_t narr);
 size_t ws_u32_kv(uint64_t ntot, uint32_t narr);
 size_t ws_u64(uint64_t ntot, uint32_t narr);
 size_t ws_u64_kv(uint64_t ntot, uint32_t narr);
+// Dispatch by key type, and the device error word as a DFR status (dfr_api.cu).
+int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st);
+int ws_typed(int key_type, uint64_t ntot, uint32_t narr, size_t* bytes);
+int map_device_status(uint32_t err);
 
 }  // namespace dfr

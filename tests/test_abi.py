@@ -89,3 +89,21 @@ def test_status_strings_and_counters(lib):
         assert dfr.dfr_status_string(code)
     assert dfr.dfr_launch_count() >= 0
     assert dfr.dfr_set_debug(0, False) == dfr.DFR_OK
+
+
+def test_server_host_checks(lib):
+    """Argument checks of the served form that return before any CUDA call."""
+    h = ctypes.c_void_p(0)
+    assert lib.dfr_server_create(None, 0, 1 << 20, 1) == dfr.DFR_ERR_INVALID_ARG
+    assert lib.dfr_server_create(ctypes.byref(h), 0, 100, 1) == dfr.DFR_ERR_INVALID_ARG  # budget < 4096
+    assert lib.dfr_server_create(ctypes.byref(h), 0, 1 << 20, 0) == dfr.DFR_ERR_INVALID_ARG
+    assert lib.dfr_server_create(ctypes.byref(h), 0, 1 << 20, dfr.DFR_SERVER_MAX_STREAMS + 1) == dfr.DFR_ERR_INVALID_ARG
+    assert h.value is None
+    t = ctypes.c_uint64(0)
+    seg = dfr.dfr_segment_t(dfr.DFR_U32, 0x1000, 0, 0, 0, 10)
+    assert lib.dfr_submit(None, ctypes.byref(seg), ctypes.byref(t)) == dfr.DFR_ERR_INVALID_ARG
+    d = ctypes.c_int(0)
+    assert lib.dfr_poll(None, 1, ctypes.byref(d), None) == dfr.DFR_ERR_INVALID_ARG
+    assert lib.dfr_wait(None, 1, None) == dfr.DFR_ERR_INVALID_ARG
+    assert lib.dfr_server_stats(None, None, None, None) == dfr.DFR_ERR_INVALID_ARG
+    assert lib.dfr_server_destroy(None) == dfr.DFR_ERR_INVALID_ARG
