@@ -53,9 +53,15 @@ WORKLOADS = {
     "kv_u64_2^27": dict(kind="plain", key="u64kv", n=1 << 27, dists=list(synth.U64_DISTRIBUTIONS)),
     # a smaller case (still larger than L2) for full ncu captures
     "plain_u32_2^26": dict(kind="plain", key="u32", n=1 << 26, dists=["uniform"]),
+    # 4096 u32 arrays, log-uniform sizes over [2^8, 2^20], uniform or Zipf per array
+    "batch_u32_4096": dict(kind="batch", key="u32", count=4096, lo=1 << 8, hi=1 << 20),
+    # Poisson stream of requests, log-uniform sizes over [2^10, 2^24], 70% u32 / 30% u64+u32
+    "served_mixed": dict(kind="served", key="mixed", requests=100_000, lo=1 << 10, hi=1 << 24,
+                         budget=16 << 30, loads=[0.25, 0.5, 0.75, 1.0]),
 }
 DEFAULT_WORKLOAD = "plain_u32_2^28"
-SEED_OFFSET = {"plain_u32_2^28": 20, "plain_u32_1M": 1, "kv_u64_2^27": 30, "plain_u32_2^26": 20}
+SEED_OFFSET = {"plain_u32_2^28": 20, "plain_u32_1M": 1, "kv_u64_2^27": 30, "plain_u32_2^26": 20,
+               "batch_u32_4096": 40, "served_mixed": 50}
 
 
 def kernel_source_sha() -> str:
@@ -194,6 +200,8 @@ def run_reference(args, wl, world, rank):
     import oracle
 
     oracle.build()
+    if wl["kind"] != "plain":
+        return run_reference_forms(args, wl)
     sample_n = min(wl["n"], args.cpu_sample)
     sub = dict(wl)
     sub["n"] = sample_n
@@ -220,6 +228,443 @@ def run_reference(args, wl, world, rank):
     return 0
 
 
+def profile_one(dfr, fn, stream):
+    """Run fn() once with per-launch CUDA events; returns {kind: (ms, launches)}."""
+    import torch
+
+    dfr.dfr_profile_enable(True)
+    dfr.dfr_profile_read()
+    fn()
+    torch.cuda.synchronize()
+    prof = dfr.dfr_profile_read()
+    dfr.dfr_profile_enable(False)
+    return {k: v for k, v in prof.items() if v[1]}
+
+
+def dominant_roofline(prof, stats, rec, peak, peak_kind):
+    """Roofline of the kernel kind with the largest share among the two that
+    move records (the scatter and the CTA sort): algorithmic bytes = a read
+    and a write of every record it handles, over its measured time."""
+    moved = {"scatter": 2 * rec * sum(stats["level_keys"]),
+             "ctasort": 2 * rec * stats["cta_keys"]}
+    cand = [k for k in moved if k in prof and prof[k][0] > 0]
+    if not cand:
+        return None
+    k = max(cand, key=lambda x: prof[x][0])
+    ms, launches = prof[k]
+    achieved = moved[k] / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_" + k, "peak_source": peak_kind,
+            "algorithmic_bytes_per_launch": moved[k] / max(1, launches)}
+
+
+def batch_inputs(wl):
+    arrays, kinds = synth.batch_u32(wl["count"], synth.BASE_SEED + SEED_OFFSET["batch_u32_4096"], wl["lo"], wl["hi"])
+    return arrays, kinds
+
+
+def run_batch(args, wl, dfr, dev, world, rank):
+    """Many arrays: one dfr_sort_batch launch sequence against one plain
+    dfr_sort_u32 call per array on one stream, uncaptured and captured in a
+    CUDA graph.  Every arm sorts the same arrays, restored from a pristine copy
+    and with L2 flushed before each timed repetition (untimed)."""
+    import torch
+
+    arrays, kinds = batch_inputs(wl)
+    sizes = [a.size for a in arrays]
+    offs, pos = [], 0
+    for n in sizes:
+        offs.append(pos)
+        pos += (n + 63) // 64 * 64  # 256-byte aligned starts
+    total_keys = int(sum(sizes))
+    host = np.zeros(pos, dtype=np.uint32)
+    for o, a in zip(offs, arrays):
+        host[o:o + a.size] = a
+    stream = torch.cuda.current_stream(dev)
+    pristine = dfr.to_device(host, dev)
+    work = torch.empty_like(pristine)
+    kbuf = torch.empty_like(pristine)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    base, bbase = work.data_ptr(), kbuf.data_ptr()
+    segs = [(dfr.DFR_U32, base + 4 * o, 0, bbase + 4 * o, 0, n) for o, n in zip(offs, sizes)]
+    wsb = dfr.dfr_batch_workspace_bytes(segs)
+    ws = torch.zeros(wsb, dtype=torch.uint8, device=dev)
+    pwsb = dfr.dfr_workspace_bytes(dfr.DFR_U32, max(sizes))
+    pws = torch.zeros(pwsb, dtype=torch.uint8, device=dev)
+
+    def restore():
+        work.copy_(pristine)
+        flush.fill_(1)
+
+    def batched():
+        dfr.check(dfr.dfr_sort_batch(segs, ws, wsb, stream), "dfr_sort_batch")
+
+    def plain():
+        st = int(stream.cuda_stream)
+        for o, n in zip(offs, sizes):
+            rc = dfr.dfr_sort_u32(base + 4 * o, bbase + 4 * o, n, pws, pwsb, st)
+            if rc:
+                dfr.check(rc, "dfr_sort_u32")
+
+    def timed(fn, steps):
+        out = []
+        for _ in range(steps):
+            restore()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return out
+
+    def verify(tag):
+        got = dfr.to_numpy(work, np.uint32)
+        for i in range(0, len(arrays), 97):  # a sample checked against the host arrays
+            o, a = offs[i], arrays[i]
+            seg = got[o:o + a.size]
+            if not (np.all(seg[1:] >= seg[:-1]) and np.array_equal(np.sort(a), seg)):
+                raise RuntimeError("%s: array %d is not the sorted input" % (tag, i))
+
+    # warm-up (also fills the launch-grid cache before graph capture)
+    for _ in range(args.warmup):
+        timed(batched, 1)
+    if dfr.dfr_last_device_status(ws, stream) != dfr.DFR_OK:
+        raise RuntimeError("device status after batched warm-up")
+    verify("batched")
+    timed(plain, 1)
+    verify("plain")
+
+    graph = torch.cuda.CUDAGraph()
+    restore()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+        cap_stream = torch.cuda.current_stream()
+        st = int(cap_stream.cuda_stream)
+        for o, n in zip(offs, sizes):
+            dfr.check(dfr.dfr_sort_u32(base + 4 * o, bbase + 4 * o, n, pws, pwsb, st), "capture")
+    timed(graph.replay, 1)
+    verify("graph")
+
+    clocks = ClockSampler(dev.index or 0)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = dfr.dfr_launch_count()
+    t_batch = timed(batched, args.steps)
+    launches = dfr.dfr_launch_count() - l0
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    t_plain = timed(plain, max(1, min(args.steps, 3)))
+    t_graph = timed(graph.replay, max(1, min(args.steps, 3)))
+    ms = reduce_max([statistics.mean(t_batch)], world, dev)[0]
+    value = world * total_keys / (ms * 1e-3) / 1e9
+    ms_plain = statistics.median(t_plain)
+    ms_graph = statistics.median(t_graph)
+
+    restore()
+    prof = profile_one(dfr, batched, stream)
+    stats = dfr.dfr_get_stats(ws, stream)
+    peak, peak_kind = measured_peaks()
+    roof = dominant_roofline(prof, stats, 4, peak, peak_kind)
+
+    e2e = None
+    if not args.no_e2e:
+        hin = torch.from_numpy(host.view(np.int32)).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        tt = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            work.copy_(hin, non_blocking=True)
+            batched()
+            hout.copy_(work, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            tt.append(e0.elapsed_time(e1))
+        ems = reduce_max([statistics.mean(tt)], world, dev)[0]
+        e2e = {"value": world * total_keys / (ems * 1e-3) / 1e9, "unit": "Gkeys/s",
+               "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": int(host.nbytes), "ms_per_step": ems}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = cpu_batch_time(arrays, args.cpu_sample)
+    if rank == 0:
+        line = {
+            "metric": "Gkeys/s", "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.workload, "arrays": len(arrays), "total_keys": total_keys,
+                       "sizes": "log-uniform [2^8, 2^20]", "keys": "uniform or Zipf(1.1) per array",
+                       "uniform_arrays": kinds.count("uniform"),
+                       "l2": "flushed (256 MiB write) before every repetition",
+                       "inputs": "restored from a pristine device copy before every repetition (untimed)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "batched_vs_plain": {
+                "batched_gkeys_s": value / world,
+                "plain_uncaptured_gkeys_s": total_keys / (ms_plain * 1e-3) / 1e9,
+                "plain_graph_gkeys_s": total_keys / (ms_graph * 1e-3) / 1e9,
+                "plain_uncaptured_ms": ms_plain, "plain_graph_ms": ms_graph, "batched_ms": ms / 1,
+                "speedup_vs_uncaptured": ms_plain / ms, "speedup_vs_graph": ms_graph / ms},
+            "sort_roofline_frac": stats["model_bytes"] / (ms * 1e-3) / 1e9 / peak,
+            "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()},
+            "plan": {k: stats[k] for k in ("levels", "cta_keys", "wsort_keys", "tiny_keys", "const_keys",
+                                           "cta_buckets", "wsort_buckets", "model_bytes")},
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_batch_time(arrays, sample_keys):
+    """The oracle, single-threaded, on the first arrays up to sample_keys keys."""
+    import oracle
+
+    keys, t0 = 0, time.perf_counter()
+    count = 0
+    for a in arrays:
+        if keys >= sample_keys:
+            break
+        oracle.sort_u32(a)
+        keys += a.size
+        count += 1
+    dt = time.perf_counter() - t0
+    return {"value": keys / dt / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "sample": "the first %d of the arrays (%d keys, %.1f s)" % (count, keys, dt)}
+
+
+class _Ring:
+    """First-in first-out arena for the client's request buffers: blocks are
+    handed out in order and returned in the same order."""
+
+    def __init__(self, size):
+        import collections
+
+        self.size = size
+        self.live = collections.deque()  # (offset, bytes) in allocation order
+
+    def alloc(self, nbytes):
+        nbytes = (nbytes + 255) // 256 * 256
+        if not self.live:
+            off = 0 if nbytes <= self.size else None
+        else:
+            tail = self.live[0][0]
+            head = self.live[-1][0] + self.live[-1][1]
+            if head > tail:
+                off = head if self.size - head >= nbytes else (0 if tail >= nbytes else None)
+            else:  # wrapped: free space is [head, tail)
+                off = head if tail - head >= nbytes else None
+        if off is not None:
+            self.live.append((off, nbytes))
+        return off
+
+    def free_oldest(self):
+        self.live.popleft()
+
+
+def served_pass(dfr, srv, gen, arena, sizes, kvs, seed, rate, ring_bytes, events):
+    """One pass of the request stream.  rate = None: closed loop (submit as
+    fast as buffers allow); else Poisson arrivals at `rate` requests/s.
+    Each request's keys are generated on the device at its arrival (SplitMix64
+    on the producer stream `gen`), then submitted with an event to wait on.
+    Returns (latencies in us from the scheduled arrival, wall seconds from the
+    first arrival to the last completion, keys)."""
+    import collections
+
+    R = len(sizes)
+    g = np.random.Generator(np.random.PCG64(seed + 7))
+    arrivals = np.cumsum(g.exponential(1.0 / rate, R)) if rate else np.zeros(R)
+    ring = _Ring(ring_bytes)
+    base = arena.data_ptr()
+    outstanding = collections.deque()
+    lats = np.zeros(R)
+    t0 = time.perf_counter()
+    t_last = t0
+    gst = int(gen.cuda_stream)
+
+    def retire(block):
+        nonlocal t_last
+        while outstanding:
+            r, t, t_sched, t_call = outstanding[0]
+            if block:
+                rc, lat = dfr.dfr_wait(srv, t)
+                done = True
+            else:
+                rc, done, lat = dfr.dfr_poll(srv, t)
+            if not done:
+                return
+            if rc != dfr.DFR_OK:
+                raise RuntimeError("request %d: %s" % (r, dfr.dfr_status_string(rc)))
+            lats[r] = lat + (t_call - t_sched) * 1e6
+            t_last = max(t_last, t_call + lat * 1e-6)
+            ring.free_oldest()
+            outstanding.popleft()
+            block = False
+
+    for r in range(R):
+        n = int(sizes[r])
+        kv = bool(kvs[r])
+        kb = 8 if kv else 4
+        need = n * kb + (n * 4 if kv else 0) + 256
+        t_sched = t0 + arrivals[r]
+        while time.perf_counter() < t_sched:
+            retire(False)
+        while True:
+            off = ring.alloc(need)
+            if off is not None:
+                break
+            retire(True)
+        kp = base + off
+        vp = base + off + ((n * kb + 255) // 256 * 256) if kv else 0
+        kt = dfr.DFR_U64_KV if kv else dfr.DFR_U32
+        dfr.check(dfr.dfr_fill_splitmix64(kt, kp, vp, n, synth.request_seed(seed, r), gst), "fill")
+        ev = events[r % len(events)]
+        ev.record(gen)
+        t_call = time.perf_counter()
+        rc, t = dfr.dfr_submit_after(srv, (kt, kp, vp, 0, 0, n), ev)
+        if rc != dfr.DFR_OK:
+            raise RuntimeError("submit: %s" % dfr.dfr_status_string(rc))
+        outstanding.append((r, t, t_sched, t_call))
+        retire(False)
+    retire(True)
+    while outstanding:
+        retire(True)
+    keys = int(np.sum(sizes))
+    return lats, t_last - t0, keys
+
+
+def run_served(args, wl, dfr, dev, world, rank):
+    """Served form: a Poisson stream of sort requests through dfr_submit, at
+    offered loads of 25/50/75/100% of the saturated (closed-loop) served
+    throughput, against the same stream served first-in first-out with one
+    plain launch sequence per request (the same server with coalescing off and
+    one stream)."""
+    import torch
+
+    R = args.requests or wl["requests"]
+    seed = synth.BASE_SEED + SEED_OFFSET["served_mixed"]
+    sizes, kvs = synth.served_stream(R, seed, wl["lo"], wl["hi"])
+    mean_n = float(np.mean(sizes))
+    ring_bytes = 32 << 30
+    arena = torch.empty(ring_bytes, dtype=torch.uint8, device=dev)
+    gen = torch.cuda.Stream(dev)
+    events = [torch.cuda.Event() for _ in range(1024)]
+    torch.cuda.synchronize()
+
+    def make_server(batched):
+        srv = dfr.dfr_server_create(dev.index or 0, wl["budget"], args.serve_streams if batched else 1)
+        if not batched:  # back-to-back plain launches, in arrival order, on one stream
+            dfr.check(dfr.dfr_server_set_limits(srv, 1, dfr.DFR_SERVER_MAX_INFLIGHT), "limits")
+        return srv
+
+    def one(batched, rate, count=None):
+        srv = make_server(batched)
+        try:
+            c = count or R
+            lats, wall, keys = served_pass(dfr, srv, gen, arena, sizes[:c], kvs[:c], seed, rate, ring_bytes, events)
+            st = dfr.dfr_server_stats(srv)
+        finally:
+            dfr.dfr_server_destroy(srv)
+        return {"gkeys_s": keys / wall / 1e9, "p50_us": float(np.percentile(lats, 50)),
+                "p99_us": float(np.percentile(lats, 99)), "mean_us": float(np.mean(lats)), "wall_s": wall,
+                "requests": int(len(lats)), "batches": st["batches"]}
+
+    # warm-up: a short closed-loop pass of each arm
+    for _ in range(max(1, args.warmup)):
+        one(True, None, min(R, 500))
+        one(False, None, min(R, 200))
+
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    l0 = dfr.dfr_launch_count()
+    closed = one(True, None)
+    peak_keys_s = closed["gkeys_s"] * 1e9
+    loads = {}
+    for L in wl["loads"]:
+        rate = L * peak_keys_s / mean_n
+        loads["%d%%" % round(100 * L)] = {"offered_req_s": rate, "offered_gkeys_s": L * peak_keys_s / 1e9,
+                                          "batched": one(True, rate),
+                                          "fifo_plain": one(False, rate)}
+    launches = dfr.dfr_launch_count() - l0
+    clk = clocks.stop()
+    closed_plain = one(False, None, min(R, 20_000))
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = cpu_served_time(wl, args.cpu_sample, R)
+    if rank == 0:
+        full = loads["100%"]
+        line = {
+            "metric": "Gkeys/s", "value": closed["gkeys_s"], "unit": "Gkeys/s", "n_gpus": world,
+            "steps": 1, "warmup": args.warmup, "ms_per_step": closed["wall_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32 | u64+u32", "data": "synthetic",
+            "config": {"workload": args.workload, "requests": R, "sizes": "log-uniform [2^10, 2^24]",
+                       "mix": "70% u32 keys only, 30% u64 keys + u32 payloads", "keys": "uniform (SplitMix64)",
+                       "budget_bytes": wl["budget"], "server_streams": args.serve_streams,
+                       "arrivals": "Poisson", "l2": "inputs regenerated per request (not resident in L2)"},
+            "roofline": None, "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches, "clocks": clk,
+            "closed_loop": {"batched": closed, "fifo_plain": closed_plain},
+            "loads": loads,
+            "p50_us_at_100pct": full["batched"]["p50_us"], "p99_us_at_100pct": full["batched"]["p99_us"],
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_served_time(wl, sample_keys, requests=0):
+    """The oracle, single-threaded, on the first requests of the served stream
+    (keys regenerated on the host) up to sample_keys keys."""
+    import oracle
+
+    R = requests or wl["requests"]
+    seed = synth.BASE_SEED + SEED_OFFSET["served_mixed"]
+    sizes, kvs = synth.served_stream(R, seed, wl["lo"], wl["hi"])
+    keys, cnt, dt = 0, 0, 0.0
+    for r in range(R):
+        if keys >= sample_keys:
+            break
+        n = int(sizes[r])
+        if kvs[r]:
+            k, v = synth.splitmix64(synth.request_seed(seed, r), n), synth.index_payload(n)
+            t0 = time.perf_counter()
+            oracle.sort_u64_kv(k, v)
+        else:
+            k = synth.splitmix64_u32(synth.request_seed(seed, r), n)
+            t0 = time.perf_counter()
+            oracle.sort_u32(k)
+        dt += time.perf_counter() - t0
+        keys += n
+        cnt += 1
+    return {"value": keys / dt / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "sample": "the first %d requests of the stream (%d keys, %.1f s of sorting, keys regenerated on "
+                      "the host)" % (cnt, keys, dt)}
+
+
+def run_reference_forms(args, wl):
+    """Reference arm of the batch and served workloads: the oracle on a
+    bounded sample (the first arrays / requests), once per step."""
+    if wl["kind"] == "batch":
+        arrays, _ = batch_inputs(wl)
+        fn = lambda: cpu_batch_time(arrays, args.cpu_sample)  # noqa: E731
+    else:
+        fn = lambda: cpu_served_time(wl, args.cpu_sample, args.requests)  # noqa: E731
+    for _ in range(args.warmup):
+        fn()
+    runs = [fn() for _ in range(args.steps)]
+    value = statistics.mean(r["value"] for r in runs)
+    line = {
+        "impl": "reference", "metric": "Gkeys/s", "value": value, "unit": "Gkeys/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32" if wl["kind"] == "batch" else "u32 | u64+u32",
+        "data": "synthetic", "config": {"workload": args.workload},
+        "cpu_baseline": dict(runs[-1], value=value),
+        "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def config_of(name, wl):
     return {"workload": name, "n_per_array": wl["n"], "arrays_per_step": len(wl["dists"]),
             "distributions": wl["dists"], "key": wl["key"], "l2": "flushed (256 MiB write) before every sort",
@@ -236,9 +681,11 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 26)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dists", default="", help="comma-separated subset of the workload's distributions")
+    ap.add_argument("--requests", type=int, default=0, help="served workload: requests per pass")
+    ap.add_argument("--serve-streams", type=int, default=4, help="served workload: server streams")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
-    if args.dists:
+    if args.dists and "dists" in wl:
         wl["dists"] = [d for d in args.dists.split(",") if d in wl["dists"]]
     rank, world, local = dist_setup()
 
@@ -259,6 +706,10 @@ def main():
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    if wl["kind"] == "batch":
+        return run_batch(args, wl, dfr, dev, world, rank)
+    if wl["kind"] == "served":
+        return run_served(args, wl, dfr, dev, world, rank)
     stream = torch.cuda.current_stream(dev)
     n = wl["n"]
     kv = wl["key"] == "u64kv"

@@ -232,6 +232,24 @@ int dfr_server_create(dfr_server_t** server, int device, size_t mem_budget_bytes
  * budget; DFR_ERR_BUSY once the server is being destroyed. */
 int dfr_submit(dfr_server_t* server, const dfr_segment_t* req, uint64_t* ticket);
 
+/* dfr_submit_after -- as dfr_submit, for inputs still being produced on the
+ * device: the stream that sorts the request first waits on `ready_event` (a
+ * cudaEvent_t recorded by the caller after the work that writes the
+ * request's buffers; NULL = no wait).  The event must stay alive until the
+ * request is done; recording it again before then is allowed only for later
+ * work of the same stream (the wait then covers that work too). */
+int dfr_submit_after(dfr_server_t* server, const dfr_segment_t* req, void* ready_event, uint64_t* ticket);
+
+/* dfr_server_set_limits -- `max_batch`: cap on requests coalesced into one
+ * launch sequence (1 .. 4096, default 4096); 1 serves every request alone
+ * with the plain single-array launch sequence.  `max_inflight_per_stream`:
+ * batches enqueued on one stream before the server waits for one of them to
+ * complete (1 .. DFR_SERVER_MAX_INFLIGHT, default 1); with 1 stream,
+ * max_batch 1 and a deep in-flight limit, requests are sorted by back-to-back
+ * plain launches in arrival order. */
+#define DFR_SERVER_MAX_INFLIGHT 64
+int dfr_server_set_limits(dfr_server_t* server, uint32_t max_batch, uint32_t max_inflight_per_stream);
+
 /* dfr_poll -- *done = 1 once the request's sort has completed on the device;
  * then *latency_us (may be NULL) = completion time - submission time in
  * microseconds, the ticket is released and the request's status is returned
@@ -250,6 +268,21 @@ int dfr_server_stats(dfr_server_t* server, uint64_t* batches, uint64_t* pending,
 /* dfr_server_destroy -- finish every queued request, then free the pool, the
  * streams and the server.  Tickets not yet polled are released. */
 int dfr_server_destroy(dfr_server_t* server);
+
+/* ---------------------------------------------------- synthetic inputs -- */
+
+/*
+ * dfr_fill_splitmix64 -- write n seeded pseudo-random keys on the device (for
+ * benchmarks and tests; not part of the sort).  Key i is output i of the
+ * SplitMix64 generator (Steele, Lea and Flood, OOPSLA 2014) seeded with
+ * `seed`: z = seed + (i+1)*0x9E3779B97F4A7C15, then the generator's mixing
+ * function; u32 keys take its high 32 bits.  For the kv key types
+ * vals[i] = i (the original index); `vals` is ignored otherwise.
+ * Asynchronous on `stream`.  Errors: DFR_ERR_INVALID_ARG for an unknown key
+ * type, n > DFR_MAX_N, or a null or misaligned pointer.
+ */
+int dfr_fill_splitmix64(int key_type, void* keys, uint32_t* vals, uint64_t n, uint64_t seed,
+                        dfr_stream_t stream);
 
 /* ---------------------------------------------------- debug and profiling -- */
 

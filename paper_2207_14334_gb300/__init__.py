@@ -38,6 +38,7 @@ DFR_NOALLOC_MAX_N = 1 << 20
 DFR_PROFILE_KINDS = 10
 DFR_STATS_MAX_LEVELS = 16
 DFR_SERVER_MAX_STREAMS = 64
+DFR_SERVER_MAX_INFLIGHT = 64
 
 KEY_BYTES = {DFR_U32: 4, DFR_U64: 8, DFR_U64_KV: 8, DFR_U32_KV: 4}
 HAS_VALS = {DFR_U32: False, DFR_U64: False, DFR_U64_KV: True, DFR_U32_KV: True}
@@ -84,6 +85,9 @@ _SIGNATURES = {
     "dfr_sort_batch": (ctypes.c_int, [ctypes.POINTER(dfr_segment_t), _u32, _vp, _sz, _vp]),
     "dfr_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _sz, ctypes.c_int]),
     "dfr_submit": (ctypes.c_int, [_vp, ctypes.POINTER(dfr_segment_t), ctypes.POINTER(_u64)]),
+    "dfr_submit_after": (ctypes.c_int, [_vp, ctypes.POINTER(dfr_segment_t), _vp, ctypes.POINTER(_u64)]),
+    "dfr_server_set_limits": (ctypes.c_int, [_vp, _u32, _u32]),
+    "dfr_fill_splitmix64": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _u64, _u64, _vp]),
     "dfr_poll": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "dfr_wait": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(ctypes.c_double)]),
     "dfr_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
@@ -239,6 +243,26 @@ def dfr_submit(server: int, seg) -> tuple:
     t = _u64(0)
     rc = load().dfr_submit(_vp(server), arr, ctypes.byref(t))
     return int(rc), int(t.value)
+
+
+def dfr_submit_after(server: int, seg, ready_event=None) -> tuple:
+    """As dfr_submit; the sorting stream first waits on `ready_event` (a
+    torch.cuda.Event, a raw cudaEvent_t int, or None)."""
+    arr = _segments([seg])
+    t = _u64(0)
+    ev = 0 if ready_event is None else (ready_event if isinstance(ready_event, int) else int(ready_event.cuda_event))
+    rc = load().dfr_submit_after(_vp(server), arr, _vp(ev), ctypes.byref(t))
+    return int(rc), int(t.value)
+
+
+def dfr_server_set_limits(server: int, max_batch: int, max_inflight_per_stream: int = 1) -> int:
+    return load().dfr_server_set_limits(_vp(server), int(max_batch), int(max_inflight_per_stream))
+
+
+def dfr_fill_splitmix64(key_type: int, keys, vals, n: int, seed: int, stream=None) -> int:
+    """Seeded SplitMix64 keys on the device (and vals[i] = i for kv types)."""
+    return load().dfr_fill_splitmix64(int(key_type), _ptr(keys), _ptr(vals), int(n), int(seed) & (2 ** 64 - 1),
+                                      _stream(stream))
 
 
 def dfr_poll(server: int, ticket: int) -> tuple:

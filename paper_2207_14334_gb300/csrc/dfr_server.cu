@@ -83,14 +83,15 @@ class Pool {
 struct Request {
   uint64_t ticket = 0;
   dfr_segment_t seg{};
+  cudaEvent_t ready = nullptr;  // the batch's stream waits on it before sorting
   double t_submit = 0.0;
   double latency_us = 0.0;
   int status = DFR_OK;
   bool done = false;
 };
 
-constexpr size_t kMaxBatch = 4096;  // requests per batched launch sequence
-constexpr int kStatusSlot = 64;     // bytes of pinned memory per stream for the error word
+constexpr size_t kMaxBatch = 4096;  // default cap on requests per batched launch sequence
+constexpr int kStatusSlot = 64;     // bytes of pinned memory per batch for its error word
 
 size_t key_bytes_of(int kt) { return (kt == DFR_U64 || kt == DFR_U64_KV) ? 8u : 4u; }
 bool has_vals(int kt) { return kt == DFR_U64_KV || kt == DFR_U32_KV; }
@@ -119,6 +120,7 @@ struct dfr_server {
     std::vector<Request*> reqs;
     size_t off = 0, bytes = 0;  // pool block
     int stream = 0;
+    int slot = 0;  // error-word slot in status_host
     int launch_status = DFR_OK;
     // written by the completion host function under done_mu
     bool finished = false;
@@ -129,10 +131,11 @@ struct dfr_server {
   int device = 0;
   size_t budget = 0;
   unsigned char* base = nullptr;
-  uint32_t* status_host = nullptr;  // pinned, one slot per stream
+  uint32_t* status_host = nullptr;  // pinned, one error-word slot per batch slot
+  std::vector<int> free_slots;
   Pool* pool = nullptr;
   std::vector<cudaStream_t> streams;
-  std::vector<bool> stream_busy;
+  std::vector<uint32_t> stream_load;  // batches in flight per stream
 
   std::mutex mu;  // everything below, except the Batch completion fields
   std::condition_variable cv;
@@ -141,6 +144,8 @@ struct dfr_server {
   std::vector<Batch*> inflight;
   uint64_t next_ticket = 1;
   uint64_t launched_batches = 0;
+  size_t max_batch = kMaxBatch;
+  uint32_t max_inflight = 1;  // batches in flight per stream
   bool stop = false;
 
   std::mutex done_mu;
@@ -170,11 +175,8 @@ void CUDART_CB dfr_server::on_done(void* p) {
 dfr_server::Batch* dfr_server::form_batch(std::vector<dfr_segment_t>* segs) {
   int st = -1;
   for (size_t i = 0; i < streams.size(); ++i)
-    if (!stream_busy[i]) {
-      st = (int)i;
-      break;
-    }
-  if (st < 0 || pending.empty()) return nullptr;
+    if (stream_load[i] < max_inflight && (st < 0 || stream_load[i] < stream_load[(size_t)st])) st = (int)i;
+  if (st < 0 || pending.empty() || free_slots.empty()) return nullptr;
   const int kt = pending.front()->seg.key_type;
   const size_t room = pool->largest();
   std::vector<Request*> take;
@@ -182,7 +184,7 @@ dfr_server::Batch* dfr_server::form_batch(std::vector<dfr_segment_t>* segs) {
   size_t scratch = 0, total = 0;
   for (Request* r : pending) {
     if (r->seg.key_type != kt) continue;
-    if (take.size() >= kMaxBatch) break;
+    if (take.size() >= max_batch) break;
     const size_t need = ws_bytes(kt, ntot + r->seg.n, (uint32_t)take.size() + 1) + scratch + scratch_bytes(r->seg);
     if (need > room) break;  // later requests wait behind this one
     take.push_back(r);
@@ -197,7 +199,9 @@ dfr_server::Batch* dfr_server::form_batch(std::vector<dfr_segment_t>* segs) {
   b->reqs = take;
   b->bytes = total;
   b->off = pool->alloc(total);
-  stream_busy[st] = true;
+  ++stream_load[st];
+  b->slot = free_slots.back();
+  free_slots.pop_back();
   // hand out scratch after the workspace
   size_t at = b->off + ws_bytes(kt, ntot, (uint32_t)take.size());
   segs->clear();
@@ -227,14 +231,24 @@ dfr_server::Batch* dfr_server::form_batch(std::vector<dfr_segment_t>* segs) {
   return b;
 }
 
-// Enqueue the batch, the read-back of its device error word and the
-// completion host function on the batch's stream.  Runs without mu.
+// Enqueue the waits on the requests' ready events, the batch, the read-back
+// of its device error word and the completion host function on the batch's
+// stream.  A batch of one request takes the plain single-array launch
+// sequence.  Runs without mu.
 void dfr_server::launch(Batch* b, std::vector<dfr_segment_t>& segs) {
   cudaStream_t st = streams[b->stream];
-  uint32_t* slot = status_host + (size_t)b->stream * (kStatusSlot / sizeof(uint32_t));
+  uint32_t* slot = status_host + (size_t)b->slot * (kStatusSlot / sizeof(uint32_t));
   *slot = 0;
   void* ws = base + b->off;
-  int rc = dfr_sort_batch(segs.data(), (uint32_t)segs.size(), ws, b->bytes, (dfr_stream_t)st);
+  int rc = DFR_OK;
+  for (Request* r : b->reqs)
+    if (r->ready && cudaStreamWaitEvent(st, r->ready, 0) != cudaSuccess) rc = DFR_ERR_CUDA;
+  if (rc == DFR_OK) {
+    std::vector<HostArr> arrs(segs.size());
+    for (size_t i = 0; i < segs.size(); ++i)
+      arrs[i] = HostArr{segs[i].keys, segs[i].kbuf, segs[i].vals, segs[i].vbuf, segs[i].n};
+    rc = run_typed(segs[0].key_type, arrs.data(), (uint32_t)arrs.size(), arrs.size() > 1, ws, b->bytes, st);
+  }
   bool any = false;
   for (const auto& g : segs) any = any || g.n > 1;
   if (rc == DFR_OK && any && cudaMemcpyAsync(slot, ws, sizeof(uint32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -263,15 +277,16 @@ void dfr_server::retire() {
       ++i;
       continue;
     }
-    const uint32_t* slot = status_host + (size_t)b->stream * (kStatusSlot / sizeof(uint32_t));
+    const uint32_t* slot = status_host + (size_t)b->slot * (kStatusSlot / sizeof(uint32_t));
     const int st = b->launch_status != DFR_OK ? b->launch_status : map_device_status(*slot);
+    free_slots.push_back(b->slot);
     for (Request* r : b->reqs) {
       r->status = st;
       r->latency_us = t - r->t_submit;
       r->done = true;
     }
     pool->release(b->off, b->bytes);
-    stream_busy[b->stream] = false;
+    --stream_load[b->stream];
     inflight.erase(inflight.begin() + (long)i);
     delete b;
     cv.notify_all();
@@ -310,13 +325,15 @@ int dfr_server_create(dfr_server_t** out, int device, size_t mem_budget_bytes, i
   s->device = device;
   s->budget = mem_budget_bytes & ~(size_t)255;
   bool ok = cudaMalloc(&s->base, s->budget) == cudaSuccess;
-  ok = ok && cudaMallocHost(&s->status_host, (size_t)n_streams * kStatusSlot) == cudaSuccess;
+  const size_t nslots = (size_t)n_streams * DFR_SERVER_MAX_INFLIGHT;
+  ok = ok && cudaMallocHost(&s->status_host, nslots * kStatusSlot) == cudaSuccess;
+  for (size_t i = 0; ok && i < nslots; ++i) s->free_slots.push_back((int)(nslots - 1 - i));
   for (int i = 0; ok && i < n_streams; ++i) {
     cudaStream_t st;
     ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
     if (ok) {
       s->streams.push_back(st);
-      s->stream_busy.push_back(false);
+      s->stream_load.push_back(0u);
     }
   }
   if (!ok) {
@@ -332,7 +349,7 @@ int dfr_server_create(dfr_server_t** out, int device, size_t mem_budget_bytes, i
   return DFR_OK;
 }
 
-int dfr_submit(dfr_server_t* s, const dfr_segment_t* req, uint64_t* ticket) {
+int dfr_submit_after(dfr_server_t* s, const dfr_segment_t* req, void* ready_event, uint64_t* ticket) {
   if (!s || !req || !ticket) return DFR_ERR_INVALID_ARG;
   const dfr_segment_t& g = *req;
   if (g.key_type < DFR_U32 || g.key_type > DFR_U32_KV || g.n > DFR_MAX_N) return DFR_ERR_INVALID_ARG;
@@ -346,6 +363,7 @@ int dfr_submit(dfr_server_t* s, const dfr_segment_t* req, uint64_t* ticket) {
   if (ws_bytes(g.key_type, g.n, 1u) + scratch_bytes(g) > s->budget) return DFR_ERR_OVER_BUDGET;
   Request* r = new Request();
   r->seg = g;
+  r->ready = static_cast<cudaEvent_t>(ready_event);
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) {
@@ -359,6 +377,20 @@ int dfr_submit(dfr_server_t* s, const dfr_segment_t* req, uint64_t* ticket) {
     *ticket = r->ticket;
   }
   s->cv.notify_all();
+  return DFR_OK;
+}
+
+int dfr_submit(dfr_server_t* s, const dfr_segment_t* req, uint64_t* ticket) {
+  return dfr_submit_after(s, req, nullptr, ticket);
+}
+
+int dfr_server_set_limits(dfr_server_t* s, uint32_t max_batch, uint32_t max_inflight_per_stream) {
+  if (!s || max_batch < 1 || max_batch > kMaxBatch || max_inflight_per_stream < 1 ||
+      max_inflight_per_stream > DFR_SERVER_MAX_INFLIGHT)
+    return DFR_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->max_batch = max_batch;
+  s->max_inflight = max_inflight_per_stream;
   return DFR_OK;
 }
 

@@ -258,3 +258,42 @@ def batch_u32(count: int, seed, lo: int = 1 << 8, hi: int = 1 << 20):
             arrays.append(zipf_u32(n, ss[i]))
             kinds.append("zipf")
     return arrays, kinds
+
+
+# SplitMix64 (Steele, Lea and Flood, OOPSLA 2014), the counter-based
+# generator of the served-form request stream; the device library implements
+# the same definition (dfr_fill_splitmix64), so any request can be rebuilt here.
+_SM_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_SM_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_SM_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, n: int, start: int = 0) -> np.ndarray:
+    """Outputs start .. start+n-1 of the SplitMix64 stream seeded with `seed`:
+    z = seed + (i+1)*gamma, then the mixing function (uint64, wrapping)."""
+    with np.errstate(over="ignore"):
+        i = np.arange(start + 1, start + n + 1, dtype=np.uint64)
+        z = np.uint64(seed & (2 ** 64 - 1)) + i * _SM_GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _SM_M1
+        z = (z ^ (z >> np.uint64(27))) * _SM_M2
+        return z ^ (z >> np.uint64(31))
+
+
+def splitmix64_u32(seed: int, n: int) -> np.ndarray:
+    """u32 keys: the high halves of the SplitMix64 outputs."""
+    return (splitmix64(seed, n) >> np.uint64(32)).astype(np.uint32)
+
+
+def request_seed(base: int, r: int) -> int:
+    """Seed of request r of a served stream with base seed `base`."""
+    return ((base & 0xFFFFFFFF) << 32) | (r & 0xFFFFFFFF)
+
+
+def served_stream(count: int, seed, lo: int = 1 << 10, hi: int = 1 << 24, p_kv: float = 0.3):
+    """Sizes (log-uniform over [lo, hi]) and kinds (True = u64 keys with u32
+    payloads, with probability p_kv; else u32 keys only) of a request stream."""
+    g = _rng((seed, 5))
+    x = np.floor(np.exp(g.uniform(math.log(lo), math.log(hi), count)))
+    sizes = np.clip(x, lo, hi).astype(np.int64)
+    kv = g.random(count) < p_kv
+    return sizes, kv

@@ -107,3 +107,4 @@ def test_server_host_checks(lib):
     assert lib.dfr_wait(None, 1, None) == dfr.DFR_ERR_INVALID_ARG
     assert lib.dfr_server_stats(None, None, None, None) == dfr.DFR_ERR_INVALID_ARG
     assert lib.dfr_server_destroy(None) == dfr.DFR_ERR_INVALID_ARG
+    assert lib.dfr_server_set_limits(None, 1, 1) == dfr.DFR_ERR_INVALID_ARG

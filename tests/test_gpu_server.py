@@ -180,3 +180,83 @@ def test_served_destroy_finishes_pending(dfr):
     for r in reqs:
         k, _ = r.result(dfr)
         assert np.array_equal(k, oracle.sort_u32(r.a))
+
+
+def test_fill_splitmix64_matches_host_generator(dfr):
+    import torch
+
+    for n in (1, 33, 100_003):
+        k = torch.empty(n, dtype=torch.int32, device="cuda")
+        assert dfr.dfr_fill_splitmix64(dfr.DFR_U32, k, None, n, 0xABCDEF) == dfr.DFR_OK
+        assert np.array_equal(dfr.to_numpy(k, np.uint32), synth.splitmix64_u32(0xABCDEF, n))
+        k64 = torch.empty(n, dtype=torch.int64, device="cuda")
+        v = torch.empty(n, dtype=torch.int32, device="cuda")
+        assert dfr.dfr_fill_splitmix64(dfr.DFR_U64_KV, k64, v, n, 99) == dfr.DFR_OK
+        assert np.array_equal(dfr.to_numpy(k64, np.uint64), synth.splitmix64(99, n))
+        assert np.array_equal(dfr.to_numpy(v, np.uint32), synth.index_payload(n))
+
+
+def _device_stream(dfr, count, seed, lo, hi, max_batch=None, n_streams=3, inflight=1):
+    """Generate each request's keys on a producer stream at submission and
+    hand the server an event to wait on; returns the request list."""
+    import torch
+
+    sizes, kvs = synth.served_stream(count, seed, lo, hi)
+    gen = torch.cuda.Stream()
+    srv = dfr.dfr_server_create(torch.cuda.current_device(), 512 << 20, n_streams)
+    if max_batch is not None:
+        assert dfr.dfr_server_set_limits(srv, max_batch, inflight) == dfr.DFR_OK
+    bufs = [(torch.empty(int(n), dtype=torch.int64 if kv else torch.int32, device="cuda"),
+             torch.empty(int(n), dtype=torch.int32, device="cuda") if kv else None) for n, kv in zip(sizes, kvs)]
+    torch.cuda.synchronize()
+    reqs = []
+    try:
+        for r in range(count):
+            n = int(sizes[r])
+            kt = dfr.DFR_U64_KV if kvs[r] else dfr.DFR_U32
+            keys, vals = bufs[r]
+            s = synth.request_seed(seed, r)
+            assert dfr.dfr_fill_splitmix64(kt, keys, vals, n, s, stream=gen) == dfr.DFR_OK
+            ev = torch.cuda.Event()
+            ev.record(gen)
+            rc, t = dfr.dfr_submit_after(srv, (kt, keys, vals if vals is not None else 0, 0, 0, n), ev)
+            assert rc == dfr.DFR_OK
+            reqs.append((t, kt, n, s, keys, vals, ev))
+        for t, *_ in reqs:
+            rc, lat = dfr.dfr_wait(srv, t)
+            assert rc == dfr.DFR_OK and lat > 0.0
+        stats = dfr.dfr_server_stats(srv)
+    finally:
+        dfr.dfr_server_destroy(srv)
+    return reqs, stats
+
+
+def _check_stream(dfr, reqs):
+    for t, kt, n, s, keys, vals, _ in reqs:
+        if kt == dfr.DFR_U32:
+            a = synth.splitmix64_u32(s, n)
+            assert np.array_equal(dfr.to_numpy(keys, np.uint32), oracle.sort_u32(a)), (t, n)
+        else:
+            a = synth.splitmix64(s, n)
+            ek, ev = oracle.sort_u64_kv(a, synth.index_payload(n))
+            assert np.array_equal(dfr.to_numpy(keys, np.uint64), ek), (t, n)
+            assert np.array_equal(dfr.to_numpy(vals, np.uint32), ev), (t, n)
+
+
+def test_served_device_generated_stream(dfr):
+    """1,000 requests whose keys are generated on the device as they arrive
+    (70% u32, 30% u64 kv): each result equals the oracle's sort of the same
+    keys regenerated on the host."""
+    reqs, stats = _device_stream(dfr, 1000, 51, 1 << 4, 1 << 17)
+    assert stats["batches"] < len(reqs)
+    _check_stream(dfr, reqs)
+
+
+@pytest.mark.parametrize("inflight", [1, 16])
+def test_served_fifo_plain_mode(dfr, inflight):
+    """max_batch = 1 on one stream: every request is served alone by the plain
+    launch sequence, in arrival order, with the same results (also with many
+    plain launches in flight on the stream at once)."""
+    reqs, stats = _device_stream(dfr, 120, 52, 1 << 6, 1 << 18, max_batch=1, n_streams=1, inflight=inflight)
+    assert stats["batches"] == len(reqs)
+    _check_stream(dfr, reqs)

@@ -55,3 +55,21 @@ def test_batch_sizes():
     s = synth.batch_sizes(4096, 40)
     assert s.min() >= 256 and s.max() <= 1 << 20
     assert abs(np.log(s).mean() - (math.log(256) + math.log(1 << 20)) / 2) < 0.15
+
+
+def test_splitmix64_published_outputs():
+    # the first outputs of SplitMix64 seeded with 0, as published with the
+    # generator's reference implementation
+    z = synth.splitmix64(0, 3)
+    assert [int(x) for x in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    # counter-based: any window of the stream can be generated on its own
+    assert np.array_equal(synth.splitmix64(12345, 10, start=90), synth.splitmix64(12345, 100)[90:])
+    assert np.array_equal(synth.splitmix64_u32(7, 5), (synth.splitmix64(7, 5) >> np.uint64(32)).astype(np.uint32))
+
+
+def test_served_stream_shape():
+    sizes, kv = synth.served_stream(100_000, 50)
+    assert sizes.min() >= 1 << 10 and sizes.max() <= 1 << 24
+    assert abs(np.log(sizes).mean() - (math.log(1 << 10) + math.log(1 << 24)) / 2) < 0.05
+    assert abs(kv.mean() - 0.3) < 0.01
+    assert synth.request_seed(50, 3) != synth.request_seed(50, 4)
