@@ -1319,11 +1319,39 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
 //  * Otherwise: an LSD radix sort in shared memory over the bucket's varying
 //    bits only (windows of RB bits, constant bits skipped); every pass is
 //    stable except the first of a key-only sort.
+//
+// Shared memory: s_keys (the staging buffer) and, for key-only sorts, s_out
+// (the ranked output) hold CAP keys plus one 16-byte granule, so that a
+// bucket can be laid out with the same alignment as its destination and
+// leave the SM as 16-byte vector stores.
 template <class K, class V, int NT, int KPT>
 constexpr size_t ctasort_smem_bytes() {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
-  constexpr size_t CAP = (size_t)NT * KPT;
-  return CAP * sizeof(K) + (KV ? CAP * 4 : 0) + (size_t)(NT / 32) * M * 4 + M * 4;
+  constexpr size_t CAPX = (size_t)NT * KPT + 16 / sizeof(K);
+  // key-value sorts add u16 staged positions and a u16 output permutation
+  return CAPX * sizeof(K) * (KV ? 1 : 2) + (KV ? (size_t)NT * KPT * (4 + 2 + 2) : 0) + (size_t)(NT / 32) * M * 4 +
+         M * 4;
+}
+
+// Write elements [0, len) of a staged bucket to g, where element e sits at
+// b[sh + e] and sh = the element offset of g inside its 16-byte granule (so
+// b + sh + e and g + e share their alignment): 16-byte vector stores for the
+// aligned interior, single stores for the ragged ends.  b is 16-byte aligned.
+template <class K, int NT>
+__device__ __forceinline__ void store_staged(const K* b, uint32_t sh, K* g, uint32_t len) {
+  constexpr uint32_t VE = 16u / sizeof(K);
+  const uint32_t lo = min(len, (VE - sh) % VE);
+  const uint32_t nv = (len - lo) / VE;
+  const uint32_t hi = lo + nv * VE;
+  for (uint32_t v = threadIdx.x; v < nv; v += NT)
+    *reinterpret_cast<uint4*>(g + lo + v * VE) = *reinterpret_cast<const uint4*>(b + sh + lo + v * VE);
+  if (threadIdx.x < lo) g[threadIdx.x] = b[sh + threadIdx.x];
+  if (threadIdx.x < len - hi) g[hi + threadIdx.x] = b[sh + hi + threadIdx.x];
+}
+
+template <class K>
+__device__ __forceinline__ uint32_t granule_shift(const K* g) {
+  return (uint32_t)((reinterpret_cast<uintptr_t>(g) & 15u) / sizeof(K));
 }
 
 template <class K, class V, int NT, int KPT, int KPTA>
@@ -1331,7 +1359,8 @@ __device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const ui
                                                 uint32_t off, uint32_t len, bool par, K* s_keys, uint32_t* s_vals,
                                                 uint32_t* s_whist, uint32_t* s_dstart, uint32_t* s_scan,
                                                 uint32_t* s_scan16, uint32_t* s_maxc,
-                                                unsigned long long* s_orv) {
+                                                unsigned long long* s_orv, K* s_out, uint16_t* s_pos,
+                                                uint16_t* s_perm) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr int NW = NT / 32;
   constexpr int W = 8 * sizeof(K);
@@ -1378,21 +1407,42 @@ __device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const ui
     }
     return;
   }
-  if constexpr (!KV) {
+  {
     const int hb = top_bit<K>(vm), lb = low_bit<K>(vm);
     const uint32_t span = (uint32_t)(hb - lb + 1);
     const uint32_t wbits = span < (uint32_t)GB ? span : (uint32_t)GB;
     const uint32_t gshift = (uint32_t)hb + 1u - wbits;
     const uint32_t nb = 1u << wbits;
     uint32_t* cnt = s_whist;  // nb <= NW * M counters
-    for (uint32_t x = threadIdx.x; x < nb; x += NT) cnt[x] = 0u;
+    // all NW * M counters in use and 8 per thread: vector zeroing and scan
+    constexpr bool VEC_OK = (NW * M == NT * 8);
+    const bool vec = VEC_OK && nb == (uint32_t)(NW * M);
+    if (vec) {
+      uint4* c4 = reinterpret_cast<uint4*>(cnt) + threadIdx.x * 2u;
+      c4[0] = make_uint4(0u, 0u, 0u, 0u);
+      c4[1] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+      for (uint32_t x = threadIdx.x; x < nb; x += NT) cnt[x] = 0u;
+    }
     if (threadIdx.x == 0) *s_maxc = 0u;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < KPTA; ++i)
       r[i] = ((uint32_t)(i * 32) + lane < wvalid) ? atomicAdd(&cnt[(uint32_t)(k[i] >> gshift) & (nb - 1u)], 1u) : 0u;
     __syncthreads();
-    {
+    if (vec) {
+      // thread t owns counters 8t .. 8t+7
+      uint4* c4 = reinterpret_cast<uint4*>(cnt) + threadIdx.x * 2u;
+      const uint4 a = c4[0], b4 = c4[1];
+      const uint32_t p1 = a.x, p2 = p1 + a.y, p3 = p2 + a.z, p4 = p3 + a.w, p5 = p4 + b4.x, p6 = p5 + b4.y,
+                     p7 = p6 + b4.z, tot = p7 + b4.w;
+      uint32_t mx = max(max(max(a.x, a.y), max(a.z, a.w)), max(max(b4.x, b4.y), max(b4.z, b4.w)));
+      mx = warp_max(mx);
+      if (lane == 0 && mx) atomicMax(s_maxc, mx);
+      const uint32_t run = block_scan<NT>(tot, s_scan16);
+      c4[0] = make_uint4(run, run + p1, run + p2, run + p3);
+      c4[1] = make_uint4(run + p4, run + p5, run + p6, run + p7);
+    } else {
       // exclusive scan of the nb counters, EMAX consecutive ones per thread
       constexpr uint32_t EMAX = (uint32_t)(NW * M) / NT;
       const uint32_t e_per = nb >= (uint32_t)NT ? nb / NT : 1u;
@@ -1417,21 +1467,65 @@ __device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const ui
       }
     }
     __syncthreads();
-    if (span <= wbits || *s_maxc <= GMAX) {
+    if (KV && *s_maxc <= GMAX) {
+      // Stable: rank by (key, input position).  Keys and positions are staged
+      // in group order, payloads by input position; s_perm[final slot] =
+      // staged index; then keys and payloads leave in final order, coalesced.
       if (threadIdx.x == 0) atomicAdd(&ctl->group_buckets, 1ull);
+#pragma unroll
+      for (int i = 0; i < KPTA; ++i) {
+        const uint32_t x = (uint32_t)(i * 32) + lane;
+        if (x < wvalid) {
+          const uint32_t pos = cnt[(uint32_t)(k[i] >> gshift) & (nb - 1u)] + r[i];
+          if (pos < len) {
+            s_keys[pos] = k[i];
+            s_pos[pos] = (uint16_t)(wb + x);
+            if constexpr (KV) s_vals[wb + x] = v[i];
+          } else {
+            record_error(ctl, DERR_BOUNDS, ERR_SITE_CTASORT_STAGE);
+          }
+        }
+      }
+      __syncthreads();
+      for (uint32_t e = threadIdx.x; e < len; e += NT) {
+        const K key = s_keys[e];
+        const uint32_t pe = s_pos[e];
+        const uint32_t h = (uint32_t)(key >> gshift) & (nb - 1u);
+        const uint32_t gs = cnt[h];
+        const uint32_t ge = h + 1u < nb ? cnt[h + 1u] : len;
+        uint32_t rank = 0;
+        for (uint32_t jj = gs; jj < ge; ++jj) {
+          const K kj = s_keys[jj];
+          rank += (kj < key || (kj == key && (uint32_t)s_pos[jj] < pe)) ? 1u : 0u;
+        }
+        s_perm[gs + rank] = (uint16_t)e;
+      }
+      __syncthreads();
+      for (uint32_t o = threadIdx.x; o < len; o += NT) {
+        const uint32_t e = s_perm[o];
+        dst[off + o] = s_keys[e];
+        if constexpr (KV) vdst[off + o] = s_vals[s_pos[e]];
+      }
+      return;
+    }
+    if (!KV && (span <= wbits || *s_maxc <= GMAX)) {
+      if (threadIdx.x == 0) atomicAdd(&ctl->group_buckets, 1ull);
+      const uint32_t osh = granule_shift(dst + off);
+      // one counting pass covered every varying bit: the staged order is final
+      const uint32_t ssh = span <= wbits ? osh : 0u;
 #pragma unroll
       for (int i = 0; i < KPTA; ++i) {
         if ((uint32_t)(i * 32) + lane < wvalid) {
           const uint32_t pos = cnt[(uint32_t)(k[i] >> gshift) & (nb - 1u)] + r[i];
           if (pos < len)
-            s_keys[pos] = k[i];
+            s_keys[ssh + pos] = k[i];
           else
             record_error(ctl, DERR_BOUNDS, ERR_SITE_CTASORT_STAGE);
         }
       }
       __syncthreads();
       if (span <= wbits) {
-        for (uint32_t e = threadIdx.x; e < len; e += NT) dst[off + e] = s_keys[e];
+        store_staged<K, NT>(s_keys, osh, dst + off, len);
       } else {
         for (uint32_t e = threadIdx.x; e < len; e += NT) {
           const K key = s_keys[e];
@@ -1443,8 +1537,10 @@ __device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const ui
             const K kj = s_keys[jj];
             rank += (kj < key || (kj == key && jj < e)) ? 1u : 0u;
           }
-          dst[off + gs + rank] = key;
+          s_out[osh + gs + rank] = key;
         }
+        __syncthreads();
+        store_staged<K, NT>(s_out, osh, dst + off, len);
       }
       return;
     }
@@ -1512,11 +1608,16 @@ __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : 2)) k_ctasort(Ctx c) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr uint32_t CAP = (uint32_t)NT * KPT;
   constexpr int NW = NT / 32;
+  constexpr uint32_t CAPX = CAP + 16u / sizeof(K);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   K* s_keys = reinterpret_cast<K*>(smem_raw);
-  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + CAP);
+  K* s_out = s_keys + CAPX;  // key-only sorts only
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + (KV ? CAPX : 2 * CAPX));
   uint32_t* s_whist = s_vals + (KV ? CAP : 0);
   uint32_t* s_dstart = s_whist + NW * M;
+  uint16_t* s_pos = reinterpret_cast<uint16_t*>(s_dstart + M);  // key-value sorts only
+  uint16_t* s_perm = s_pos + (KV ? CAP : 0);
+  static_assert(!KV || CAP <= 65536u, "u16 positions");
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_scan16[NW];
   __shared__ uint32_t s_q, s_maxc;
@@ -1550,7 +1651,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024 ? 1 : 2)) k_ctasort(Ctx c) {
       const uint32_t kpt = (len + NT - 1) / NT;  // 1..KPT keys per lane
 #define DFR_CTA_BODY(A)                                                                                      \
   cta_sort_bucket<K, V, NT, KPT, A>(ctl, src, vsrc, dst, vdst, off, len, par, s_keys, s_vals, s_whist, s_dstart, \
-                                    s_scan, s_scan16, &s_maxc, s_orv)
+                                    s_scan, s_scan16, &s_maxc, s_orv, s_out, s_pos, s_perm)
       if (kpt <= 1)
         DFR_CTA_BODY(1);
       else if (kpt <= 2)
