@@ -41,11 +41,12 @@ if ROOT not in sys.path:
 
 import synth  # noqa: E402
 
-# ncu DRAM traffic of the scatter kernel (read + write bytes per key dealt),
-# taken from profiles/scatter_u32_uniform.md; valid only while the kernel
-# sources hash to SCATTER_SRC_SHA (else reported as null).
-SCATTER_NCU_BYTES_PER_KEY = None
-SCATTER_SRC_SHA = None
+# ncu DRAM traffic of the u32 key-only scatter kernel (read + write bytes per
+# key dealt), from profiles/k_scatter_u32_uniform_2^26.md; valid only for u32
+# key-only workloads while the kernel sources hash to SCATTER_SRC_SHA (else
+# the roofline's traffic is reported as null).
+SCATTER_NCU_BYTES_PER_KEY = 7.265
+SCATTER_SRC_SHA = "ddf62fa8f16f7edf"
 
 WORKLOADS = {
     "plain_u32_2^28": dict(kind="plain", key="u32", n=1 << 28, dists=list(synth.U32_DISTRIBUTIONS)),
@@ -737,7 +738,10 @@ def main():
         sorter.sort_(work, vals, n, stream)
         ev1.record(stream)
 
-    # warm-up
+    # warm-up (the clock sampler runs from here through the timed steps: the
+    # timed region alone is shorter than a few sampling periods)
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         for d in inputs:
             one_sort(d, torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -748,10 +752,8 @@ def main():
     if status != dfr.DFR_OK:
         raise RuntimeError("device status %s after warm-up" % dfr.dfr_status_string(status))
 
-    clocks = ClockSampler(local)
     barrier(world)
     torch.cuda.synchronize()
-    clocks.start()
     launches0 = dfr.dfr_launch_count()
     evs = []
     for _ in range(args.steps):
@@ -804,7 +806,7 @@ def main():
     scatter_bytes = 2 * rec * scatter_keys
     achieved = scatter_bytes / (scatter_ms * 1e-3) / 1e9 if scatter_ms > 0 else 0.0
     traffic = None
-    if SCATTER_NCU_BYTES_PER_KEY is not None and SCATTER_SRC_SHA == kernel_source_sha():
+    if SCATTER_NCU_BYTES_PER_KEY is not None and not kv and SCATTER_SRC_SHA == kernel_source_sha():
         traffic = SCATTER_NCU_BYTES_PER_KEY * scatter_keys / max(1, scatter_launches)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": "k_scatter",
@@ -866,7 +868,8 @@ def main():
             "metric": "Gkeys/s", "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32" if not kv else "u64+u32", "data": "synthetic",
-            "config": config_of(args.workload, wl), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "config": dict(config_of(args.workload, wl), clocks="sampled every 200 ms over the warm-up and timed steps"),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "per_dist": per_dist, "kernels": kernel_share,
         }
         print(json.dumps(line), flush=True)

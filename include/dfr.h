@@ -19,8 +19,8 @@
  *     in a status word inside the workspace; read them with
  *     dfr_last_device_status().
  *   - The result lands in place in `keys` (and `vals`).  `buf`/`vbuf` are the
- *     paper's extra buffer of the input's size (Section MSD: "a suitably sized
- *     extra buffer"); their contents are undefined afterwards.
+ *     paper's extra buffer, as large as the input (Section MSD); their
+ *     contents are undefined afterwards.
  *   - n == 0 and n == 1 return DFR_OK without touching the GPU.
  *   - A single array may hold at most DFR_MAX_N keys.
  *   - Ranges [keys, keys+n) and [buf, buf+n) (and the payload pair) must not
