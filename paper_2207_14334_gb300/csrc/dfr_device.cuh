@@ -159,8 +159,9 @@ struct Ctx {
   void* root;  // RootAcc<K>[narr]
   Seg* segs[2];
   uint32_t* hist[2];  // [segcap][M] per level parity
+  uint32_t* cur[2];   // key-only sorts: [segcap][M] fill cursors per level parity
   uint32_t* tile_owner;
-  uint32_t* status;   // [tilecap][M] look-back words
+  uint32_t* status;   // key-value sorts: [tilecap][M] look-back words
   Item* cta_q;
   Item* w_q;          // buckets for the warp sort
   CopyItem* copy_q;
@@ -727,6 +728,7 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
             for (uint32_t y = x << sd; y < ((x + 1) << sd); ++y) h += root[a].hist[y];
         }
         c.hist[0][(size_t)s * M + threadIdx.x] = h;
+        if constexpr (!KV) c.cur[0][(size_t)s * M + threadIdx.x] = 0u;
       }
       const uint32_t owner = s_ok ? s : NO_OWNER;
       const uint32_t ntc = ts < c.tilecap ? min(nt, c.tilecap - ts) : 0u;
@@ -738,9 +740,10 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
 
 // Level count: per segment of this level, the histogram of its digit window
 // (unless the root count already holds it) and the AND/OR of its keys (unless
-// known); it also resets the look-back words of every tile of the level.
-// Warp-granular like k_root_count: private counters flushed per segment.
-template <class K, int NT, int TILE>
+// known); for key-value sorts it also resets the look-back words of every tile
+// of the level.  Warp-granular like k_root_count: private counters flushed per
+// segment.
+template <class K, bool KV, int NT, int TILE>
 __global__ void __launch_bounds__(NT) k_level_count(Ctx c, int L) {
   constexpr int NW = NT / 32;
   __shared__ uint32_t s_h[NW * M];
@@ -774,8 +777,10 @@ __global__ void __launch_bounds__(NT) k_level_count(Ctx c, int L) {
     if (lane == 0) t = atomicAdd(&lc->hist_claim, 1u);
     t = __shfl_sync(FULL, t, 0);
     if (t >= ntiles) break;
+    if constexpr (KV) {
 #pragma unroll
-    for (int i = 0; i < M / 32; ++i) c.status[(size_t)t * M + i * 32 + lane] = 0u;
+      for (int i = 0; i < M / 32; ++i) c.status[(size_t)t * M + i * 32 + lane] = 0u;
+    }
     const uint32_t s = c.tile_owner[t];
     if (s >= c.segcap) continue;
     const Seg seg = segs[s];
@@ -854,15 +859,17 @@ __device__ __forceinline__ uint32_t look_back(const Ctx& c, uint32_t t, uint32_t
 }
 
 // Scatter (deal) of one level: every tile of every dealt segment is ranked in
-// shared memory, combined with the earlier tiles of its segment by a
-// single-pass decoupled look-back per digit, staged in digit order and
-// written to the other buffer, so each digit's run is contiguous in HBM.
+// shared memory, placed inside each bucket of its segment, staged in digit
+// order and written to the other buffer, so each digit's run is contiguous in
+// HBM.
 // Key-only: one returning shared atomic per key on block-wide counters gives
 // each key a distinct slot of its digit (order among equal digits is free;
 // lanes hitting one counter are serialised by the hardware, which measured
-// cheaper than aggregating them in software even on skewed inputs);
+// cheaper than aggregating them in software even on skewed inputs); the tile
+// claims its run of every bucket with one atomic on the bucket's fill cursor;
 // full tiles of 16-byte-aligned arrays are read with 128-bit loads.
-// Key-value: stable per-warp ranking in element order.
+// Key-value: stable per-warp ranking in element order, tiles placed in tile
+// order by a single-pass decoupled look-back per digit.
 template <class K, class V, int NT, int KPT>
 __global__ void __launch_bounds__(NT, 2) k_scatter(Ctx c, int L) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
@@ -883,6 +890,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Ctx c, int L) {
   const uint32_t ntiles = min(lc->ntiles, c.tilecap);
   const Seg* segs = ((L & 1) ? c.segs[1] : c.segs[0]);
   const uint32_t* hist = ((L & 1) ? c.hist[1] : c.hist[0]);
+  uint32_t* cur = ((L & 1) ? c.cur[1] : c.cur[0]);
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
 
   // Tiles are claimed in increasing order by running CTAs only, so the tile a
@@ -983,13 +991,21 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Ctx c, int L) {
       } else {
         tcount = s_cnt[threadIdx.x];
       }
-      st_relaxed(c.status + (size_t)t * M + threadIdx.x, (j == 0 ? FLAG_INC : FLAG_AGG) | tcount);
+      if constexpr (KV) st_relaxed(c.status + (size_t)t * M + threadIdx.x, (j == 0 ? FLAG_INC : FLAG_AGG) | tcount);
     }
     const uint32_t hcount = threadIdx.x < M ? hist[(size_t)s * M + threadIdx.x] : 0u;
     uint32_t tstart, bexcl;
     scan256x2(tcount, hcount, s_scan, tstart, bexcl);
     if (threadIdx.x < M) {
-      const uint32_t excl = look_back(c, t, seg.tile_start, threadIdx.x, tcount, &s_fail);
+      // Key-value: the tile's place among the segment's tiles in tile order
+      // (decoupled look-back), which keeps the deal stable.  Key-only: any
+      // order of tiles inside a bucket is fine, so the tile claims its run of
+      // each bucket with one atomic on the bucket's fill cursor.
+      uint32_t excl;
+      if constexpr (KV)
+        excl = look_back(c, t, seg.tile_start, threadIdx.x, tcount, &s_fail);
+      else
+        excl = tcount ? atomicAdd(&cur[(size_t)s * M + threadIdx.x], tcount) : 0u;
       s_tstart[threadIdx.x] = tstart;
       s_goff[threadIdx.x] = seg.off + bexcl + excl - tstart;
     }
@@ -1065,6 +1081,7 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
   LevelCtl* ln = &ctl->lv[L + 1];
   Seg* segs_n = ((L & 1) ? c.segs[0] : c.segs[1]);
   uint32_t* hist_n = ((L & 1) ? c.hist[0] : c.hist[1]);
+  uint32_t* cur_n = ((L & 1) ? c.cur[0] : c.cur[1]);
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t d = threadIdx.x;
 
@@ -1257,7 +1274,10 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
     // New segments / copy items: clear histogram slots, fill tile-owner maps.
     const uint32_t nn = s_new_n;
     for (uint32_t i = 0; i < nn; ++i) {
-      if (s_new_zero[i] != NO_OWNER) hist_n[(size_t)s_new_zero[i] * M + threadIdx.x] = 0u;
+      if (s_new_zero[i] != NO_OWNER) {
+        hist_n[(size_t)s_new_zero[i] * M + threadIdx.x] = 0u;
+        if constexpr (!KV) cur_n[(size_t)s_new_zero[i] * M + threadIdx.x] = 0u;
+      }
       uint32_t* owner = s_new_copy[i] ? c.copy_owner : c.tile_owner;
       const uint32_t id = s_new_owner[i];
       for (uint32_t x = threadIdx.x; x < s_new_nt[i]; x += 256) owner[s_new_ts[i] + x] = id;

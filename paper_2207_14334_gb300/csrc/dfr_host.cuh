@@ -56,7 +56,7 @@ struct Cfg<uint64_t, uint32_t> {
 };
 
 struct Layout {
-  size_t ctl, arrs, root, segs0, segs1, hist0, hist1, owner, status, ctaq, wq, copyq, copyowner, total;
+  size_t ctl, arrs, root, segs0, segs1, hist0, hist1, cur0, cur1, owner, status, ctaq, wq, copyq, copyowner, total;
   uint32_t segcap, tilecap, ctacap, wqcap, copycap, copytilecap;
 };
 
@@ -90,10 +90,16 @@ Layout make_layout(uint64_t ntot, uint32_t narr) {
   o = align256(o + (size_t)l.segcap * M * 4);
   l.hist1 = o;
   o = align256(o + (size_t)l.segcap * M * 4);
+  // key-only sorts: per (segment, digit) fill cursors of the scatter
+  constexpr bool KV = !std::is_same<V, NoVal>::value;
+  l.cur0 = o;
+  o = align256(o + (KV ? 0 : (size_t)l.segcap * M * 4));
+  l.cur1 = o;
+  o = align256(o + (KV ? 0 : (size_t)l.segcap * M * 4));
   l.owner = o;
   o = align256(o + (size_t)l.tilecap * 4);
-  l.status = o;
-  o = align256(o + (size_t)l.tilecap * M * 4);
+  l.status = o;  // key-value sorts: look-back words
+  o = align256(o + (KV ? (size_t)l.tilecap * M * 4 : 0));
   l.ctaq = o;
   o = align256(o + (size_t)l.ctacap * sizeof(Item));
   l.wq = o;
@@ -117,6 +123,8 @@ inline Ctx make_ctx(void* ws, const Layout& l, uint32_t narr) {
   c.segs[1] = reinterpret_cast<Seg*>(b + l.segs1);
   c.hist[0] = reinterpret_cast<uint32_t*>(b + l.hist0);
   c.hist[1] = reinterpret_cast<uint32_t*>(b + l.hist1);
+  c.cur[0] = reinterpret_cast<uint32_t*>(b + l.cur0);
+  c.cur[1] = reinterpret_cast<uint32_t*>(b + l.cur1);
   c.tile_owner = reinterpret_cast<uint32_t*>(b + l.owner);
   c.status = reinterpret_cast<uint32_t*>(b + l.status);
   c.cta_q = reinterpret_cast<Item*>(b + l.ctaq);
@@ -187,7 +195,7 @@ struct Kernels {
   static_assert(nlev + 1 <= MAXLV, "control blocks for every launched level");
   static constexpr auto root_count = k_root_count<K, SNT, TILE>;
   static constexpr auto root_classify = k_root_classify<K, V, TILE, TCTA, WCAP>;
-  static constexpr auto level_count = k_level_count<K, SNT, TILE>;
+  static constexpr auto level_count = k_level_count<K, !std::is_same<V, NoVal>::value, SNT, TILE>;
   static constexpr auto scatter = k_scatter<K, V, SNT, SKPT>;
   static constexpr auto classify = k_classify<K, V, TILE, TCTA, WCAP>;
   static constexpr auto ctasort = k_ctasort<K, V, CNT, CKPT>;

@@ -126,17 +126,20 @@ def test_stats_uniform_plan(dfr):
 
 
 def test_forced_timeout_reports_and_recovers(dfr):
-    """The look-back is pointed at a status word nobody sets: every waiting
-    tile must give up after the spin limit, record DFR_ERR_TIMEOUT and skip
-    its writes; the next normal call must succeed on the same context."""
+    """The look-back (used by the stable key-value deal) is pointed at a
+    status word nobody sets: every waiting tile must give up after the spin
+    limit, record DFR_ERR_TIMEOUT and skip its writes; the next normal call
+    must succeed on the same context."""
     n = 200_000
     a = synth.uniform_u32(n, 5)
+    v = synth.index_payload(n)
     try:
         dfr.dfr_set_debug(2000, True)
-        _, _, st = gpu_sort(dfr, a)
+        _, _, st = gpu_sort(dfr, a, v)
     finally:
         dfr.dfr_set_debug(0, False)
     assert st == dfr.DFR_ERR_TIMEOUT
-    k, _, st = gpu_sort(dfr, a)
+    k, vv, st = gpu_sort(dfr, a, v)
     assert st == dfr.DFR_OK
-    assert np.array_equal(k, oracle.sort_u32(a))
+    ok, ov = oracle.sort_u32_kv(a, v)
+    assert np.array_equal(k, ok) and np.array_equal(vv, ov)
