@@ -509,9 +509,11 @@ __global__ void k_init(Ctx c, ArrDesc a0, int write_a0, uint32_t root_words) {
 }
 
 // Warp-level streaming count over keys src[lo, hi): 128-bit loads (batches
-// of 8 vectors per lane in flight), warp-aggregated increments of the warp's
-// private counters `wh` at digit (key >> shift) & (M-1) when do_hist, and
-// OR / NOT-AND of the keys into orv / nandv.
+// of 8 vectors per lane in flight), one shared atomic per key on the warp's
+// private counters `wh` at digit (key >> shift) & (M-1) when do_hist (lanes
+// that hit one counter are serialised by the hardware, which measured faster
+// than aggregating them in software on every input, skewed or sorted ones
+// included), and OR / NOT-AND of the keys into orv / nandv.
 template <class K>
 __device__ __forceinline__ void warp_count_range(const K* src, uint32_t lo, uint32_t hi, uint32_t shift,
                                                  bool do_hist, uint32_t* wh, K& orv, K& nandv) {
@@ -527,7 +529,7 @@ __device__ __forceinline__ void warp_count_range(const K* src, uint32_t lo, uint
       orv |= k;
       nandv |= ~k;
     }
-    if (do_hist) warp_inc<false>(wh, digit_of(k, shift), valid);
+    if (do_hist && valid) atomicAdd(&wh[digit_of(k, shift)], 1u);
   };
   {
     const bool valid = lane < head;
@@ -871,7 +873,7 @@ __device__ __forceinline__ uint32_t look_back(const Ctx& c, uint32_t t, uint32_t
 // Key-value: stable per-warp ranking in element order, tiles placed in tile
 // order by a single-pass decoupled look-back per digit.
 template <class K, class V, int NT, int KPT>
-__global__ void __launch_bounds__(NT, 2) k_scatter(Ctx c, int L) {
+__global__ void __launch_bounds__(NT, (std::is_same<V, NoVal>::value ? 3 : 2)) k_scatter(Ctx c, int L) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr uint32_t TILE = (uint32_t)NT * KPT;
   constexpr int NW = NT / 32;
