@@ -269,6 +269,43 @@ int dfr_server_stats(dfr_server_t* server, uint64_t* batches, uint64_t* pending,
  * streams and the server.  Tickets not yet polled are released. */
 int dfr_server_destroy(dfr_server_t* server);
 
+/* ---------------------------------------------------------------- tuning -- */
+
+/*
+ * Per-size-class launch plan.  None of these knobs changes a result (the sort
+ * is exact whatever they are); they trade levels, diversion and occupancy.
+ * The built-in table comes from the project's autotuner (tune.py, measured on
+ * a GB300 and checked in); dfr_tune_set overrides an entry for this process.
+ * A call picks the entry of its key type and of the size class of its mean
+ * array length (n_total / arrays).
+ */
+typedef struct {
+    uint32_t target_log2;          /* radix window per level chosen so buckets come out near 2^target_log2
+                                      keys (6 .. 13); narrower windows mean more levels, smaller buckets */
+    uint32_t max_bits;             /* radix bits per level, 4 .. 8 (the launched levels always suffice:
+                                      a level widens its window when fewer levels remain) */
+    uint32_t warp_max;             /* diverted runs of at most this many keys go to the warp sort, larger
+                                      ones to the CTA sort (128 .. 512) */
+    uint32_t scatter_ctas_per_sm;  /* scatter grid: CTAs per SM, 0 = as many as fit */
+    uint32_t ctasort_ctas_per_sm;  /* CTA-sort grid: CTAs per SM, 0 = as many as fit */
+    uint32_t reserved[3];          /* zero */
+} dfr_tune_t;
+
+/* Size classes: 0 = mean array length below 2^12 keys, c = [2^(10+2c), 2^(12+2c)),
+ * DFR_TUNE_CLASSES-1 = 2^28 keys and above. */
+#define DFR_TUNE_CLASSES 10
+#define DFR_TUNE_WARP_MIN 128
+#define DFR_TUNE_WARP_MAX 512
+int dfr_tune_class(uint64_t mean_keys);
+
+/* dfr_tune_get / dfr_tune_set -- read or override the entry of (key_type,
+ * size_class).  dfr_tune_set validates every field (DFR_ERR_INVALID_ARG) and
+ * affects later calls of this process.  dfr_tune_reset restores the built-in
+ * table. */
+int dfr_tune_get(int key_type, int size_class, dfr_tune_t* out);
+int dfr_tune_set(int key_type, int size_class, const dfr_tune_t* t);
+int dfr_tune_reset(void);
+
 /* ---------------------------------------------------- synthetic inputs -- */
 
 /*

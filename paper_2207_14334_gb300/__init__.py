@@ -39,6 +39,9 @@ DFR_PROFILE_KINDS = 10
 DFR_STATS_MAX_LEVELS = 16
 DFR_SERVER_MAX_STREAMS = 64
 DFR_SERVER_MAX_INFLIGHT = 64
+DFR_TUNE_CLASSES = 10
+DFR_TUNE_WARP_MIN = 128
+DFR_TUNE_WARP_MAX = 512
 
 KEY_BYTES = {DFR_U32: 4, DFR_U64: 8, DFR_U64_KV: 8, DFR_U32_KV: 4}
 HAS_VALS = {DFR_U32: False, DFR_U64: False, DFR_U64_KV: True, DFR_U32_KV: True}
@@ -72,6 +75,13 @@ class dfr_stats_t(ctypes.Structure):
                 ("group_buckets", _u64)]
 
 
+class dfr_tune_t(ctypes.Structure):
+    _fields_ = [("target_log2", _u32), ("max_bits", _u32), ("warp_max", _u32), ("scatter_ctas_per_sm", _u32),
+                ("ctasort_ctas_per_sm", _u32), ("reserved", _u32 * 3)]
+
+
+TUNE_FIELDS = ("target_log2", "max_bits", "warp_max", "scatter_ctas_per_sm", "ctasort_ctas_per_sm")
+
 _SIGNATURES = {
     "dfr_workspace_bytes": (ctypes.c_int, [ctypes.c_int, _u64, ctypes.POINTER(_sz)]),
     "dfr_sort_u32": (ctypes.c_int, [_vp, _vp, _u64, _vp, _sz, _vp]),
@@ -92,6 +102,10 @@ _SIGNATURES = {
     "dfr_wait": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(ctypes.c_double)]),
     "dfr_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "dfr_server_destroy": (ctypes.c_int, [_vp]),
+    "dfr_tune_class": (ctypes.c_int, [_u64]),
+    "dfr_tune_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(dfr_tune_t)]),
+    "dfr_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(dfr_tune_t)]),
+    "dfr_tune_reset": (ctypes.c_int, []),
     "dfr_set_debug": (ctypes.c_int, [_u32, ctypes.c_int]),
     "dfr_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "dfr_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64)]),
@@ -289,6 +303,26 @@ def dfr_server_stats(server: int) -> dict:
 
 def dfr_server_destroy(server: int) -> int:
     return load().dfr_server_destroy(_vp(server))
+
+
+def dfr_tune_class(mean_keys: int) -> int:
+    return int(load().dfr_tune_class(int(mean_keys)))
+
+
+def dfr_tune_get(key_type: int, size_class: int) -> dict:
+    t = dfr_tune_t()
+    check(load().dfr_tune_get(int(key_type), int(size_class), ctypes.byref(t)), "dfr_tune_get")
+    return {f: int(getattr(t, f)) for f in TUNE_FIELDS}
+
+
+def dfr_tune_set(key_type: int, size_class: int, tune: dict) -> int:
+    """Override one entry of the launch-plan table (fields as dfr_tune_get)."""
+    t = dfr_tune_t(*(int(tune[f]) for f in TUNE_FIELDS))
+    return load().dfr_tune_set(int(key_type), int(size_class), ctypes.byref(t))
+
+
+def dfr_tune_reset() -> int:
+    return load().dfr_tune_reset()
 
 
 def dfr_set_debug(spin_limit: int = 0, force_timeout: bool = False) -> int:

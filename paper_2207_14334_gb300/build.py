@@ -38,7 +38,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "dfr.h"), __file__]
+    return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.inc")) +
+            [os.path.join(INCLUDE, "dfr.h"), __file__])
 
 
 def up_to_date() -> bool:

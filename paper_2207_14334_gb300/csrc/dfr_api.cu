@@ -32,7 +32,44 @@ std::vector<cudaEvent_t> g_prof_pending;  // start event of the launch in flight
 std::mutex g_grid_mu;
 std::map<std::pair<const void*, int>, int> g_grid_cache;
 
+// The tuning table: built-in entries written by the autotuner, overridable.
+constexpr int kKeyTypes = 4;
+const dfr_tune_t kBuiltinTune[kKeyTypes][DFR_TUNE_CLASSES] = {
+#include "dfr_tune_table.inc"
+};
+std::mutex g_tune_mu;
+dfr_tune_t g_tune[kKeyTypes][DFR_TUNE_CLASSES];
+bool g_tune_init = false;
+
+void tune_init_locked() {
+  if (g_tune_init) return;
+  for (int k = 0; k < kKeyTypes; ++k)
+    for (int c = 0; c < DFR_TUNE_CLASSES; ++c) g_tune[k][c] = kBuiltinTune[k][c];
+  g_tune_init = true;
+}
+
+bool tune_valid(const dfr_tune_t& t) {
+  if (t.target_log2 < 6 || t.target_log2 > 13) return false;
+  if (t.max_bits < 4 || t.max_bits > (uint32_t)RB) return false;
+  if (t.warp_max < DFR_TUNE_WARP_MIN || t.warp_max > DFR_TUNE_WARP_MAX) return false;
+  if (t.scatter_ctas_per_sm > 4 || t.ctasort_ctas_per_sm > 4) return false;
+  return t.reserved[0] == 0 && t.reserved[1] == 0 && t.reserved[2] == 0;
+}
+
 }  // namespace
+
+int rt_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+dfr_tune_t rt_tune(int key_type, uint64_t mean_keys) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  tune_init_locked();
+  return g_tune[key_type][dfr_tune_class(mean_keys)];
+}
 
 uint32_t rt_spin_limit() { return g_spin_limit.load(); }
 int rt_force_timeout() { return g_force_timeout.load(); }
@@ -220,6 +257,39 @@ int dfr_sort_batch(const dfr_segment_t* segs, uint32_t count, void* ws, size_t w
     a[i] = HostArr{segs[i].keys, segs[i].kbuf, segs[i].vals, segs[i].vbuf, segs[i].n};
   }
   return run_typed(kt, a.data(), count, true, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int dfr_tune_class(uint64_t mean_keys) {
+  int lg = 0;
+  while (lg < 63 && (mean_keys >> (lg + 1)) != 0) ++lg;  // floor(log2), 0 for 0 and 1
+  const int c = (lg - 10) / 2;
+  return lg < 12 ? 0 : (c >= DFR_TUNE_CLASSES ? DFR_TUNE_CLASSES - 1 : c);
+}
+
+int dfr_tune_get(int key_type, int size_class, dfr_tune_t* out) {
+  if (!out || key_type < 0 || key_type >= kKeyTypes || size_class < 0 || size_class >= DFR_TUNE_CLASSES)
+    return DFR_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  tune_init_locked();
+  *out = g_tune[key_type][size_class];
+  return DFR_OK;
+}
+
+int dfr_tune_set(int key_type, int size_class, const dfr_tune_t* t) {
+  if (!t || key_type < 0 || key_type >= kKeyTypes || size_class < 0 || size_class >= DFR_TUNE_CLASSES ||
+      !tune_valid(*t))
+    return DFR_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  tune_init_locked();
+  g_tune[key_type][size_class] = *t;
+  return DFR_OK;
+}
+
+int dfr_tune_reset(void) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune_init = false;
+  tune_init_locked();
+  return DFR_OK;
 }
 
 int dfr_set_debug(uint32_t spin_limit, int force_timeout) {

@@ -169,6 +169,10 @@ struct Ctx {
   uint32_t segcap, tilecap, ctacap, wqcap, copycap, copytilecap;
   uint32_t force_timeout;
   uint32_t nlev;      // partition levels launched
+  // launch plan of this call (none of it changes the result)
+  uint32_t target;    // buckets of about this many keys per radix window
+  uint32_t max_bits;  // radix bits per level (<= RB)
+  uint32_t warp_max;  // runs of at most this many keys go to the warp sort (<= its capacity)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -475,15 +479,14 @@ __device__ __forceinline__ uint32_t seg_tiles(uint32_t off, uint32_t len) {
 }
 
 // Digit width for a segment of `len` keys whose varying bits all lie below
-// bit `top1`, partitioned at level L of `nlev` launched levels: wide enough
-// that its buckets come out near TCTA/2 keys (the radix adapts to the segment
-// size), and at least ceil(top1 / levels left) so the remaining levels always
-// consume every bit; at most RB.
-template <int TCTA>
-__device__ __forceinline__ uint32_t window_bits(uint32_t len, uint32_t top1, int L, uint32_t nlev) {
+// bit `top1`, partitioned at level L of the c.nlev launched levels: wide
+// enough that its buckets come out near c.target keys (the radix adapts to
+// the segment size; at most c.max_bits), and at least ceil(top1 / levels
+// left) so the remaining levels always consume every bit; at most RB.
+__device__ __forceinline__ uint32_t window_bits(const Ctx& c, uint32_t len, uint32_t top1, int L) {
   uint32_t b = 1;
-  while (b < (uint32_t)RB && (len >> b) > (uint32_t)(TCTA / 2)) ++b;
-  const uint32_t left = nlev > (uint32_t)L ? nlev - (uint32_t)L : 1u;
+  while (b < c.max_bits && (len >> b) > c.target) ++b;
+  const uint32_t left = c.nlev > (uint32_t)L ? c.nlev - (uint32_t)L : 1u;
   const uint32_t bmin = (top1 + left - 1) / left;
   if (b < bmin) b = bmin;
   return b > (uint32_t)RB ? (uint32_t)RB : b;
@@ -682,7 +685,7 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
     }
     if (n <= (uint32_t)TCTA) {
       if (threadIdx.x == 0) {
-        const bool small = n <= (uint32_t)WCAP;
+        const bool small = n <= c.warp_max;
         const uint32_t q = atomicAdd(small ? &ctl->wq_count : &ctl->cta_count, 1u);
         if (q < (small ? c.wqcap : c.ctacap)) {
           (small ? c.w_q : c.cta_q)[q] = Item{0u, n, a, 0u};
@@ -695,7 +698,7 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
       continue;
     }
     const int hb = top_bit<K>(orv ^ andv);
-    const uint32_t b = window_bits<TCTA>(n, (uint32_t)hb + 1u, 0, c.nlev);
+    const uint32_t b = window_bits(c, n, (uint32_t)hb + 1u, 0);
     const uint32_t shift0 = (uint32_t)hb + 1u > b ? (uint32_t)hb + 1u - b : 0u;
     // a window inside the top byte reuses the root histogram (coarsened)
     const bool use_top = hb >= W - RB;
@@ -1159,7 +1162,7 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
         } else {
           // the window held no varying bit: move it down to the highest one
           const uint32_t top1 = (uint32_t)top_bit<K>(vm) + 1u;
-          const uint32_t b = window_bits<TCTA>(seg.len, top1, L + 1, c.nlev);
+          const uint32_t b = window_bits(c, seg.len, top1, L + 1);
           const uint32_t shift = top1 > b ? top1 - b : 0u;
           add_big(seg.off, seg.len, seg.arr, shift, top1 - shift, seg.parity, SEG_NEEDS_HIST, seg.nand, seg.orv);
         }
@@ -1184,7 +1187,7 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
           }
         } else {
           // the bucket's varying bits all lie below the parent's window
-          const uint32_t b = window_bits<TCTA>(cnt, seg.shift, L + 1, c.nlev);
+          const uint32_t b = window_bits(c, cnt, seg.shift, L + 1);
           const uint32_t shift = seg.shift > b ? seg.shift - b : 0u;
           add_big(off, cnt, seg.arr, shift, seg.shift - shift, pout, SEG_NEEDS_HIST | SEG_NEEDS_ANDOR, 0ull, 0ull);
         }
@@ -1240,7 +1243,7 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
           rcls = 2;
           atomicAdd(&s_stat[3], 1ull);
           atomicAdd(&s_stat[4], (unsigned long long)rlen);
-        } else if (rlen <= (uint32_t)WCAP) {
+        } else if (rlen <= c.warp_max) {
           rcls = 3;
           rloc = atomicAdd(&s_qn[0], 1u);
           atomicAdd(&s_stat[8], 1ull);

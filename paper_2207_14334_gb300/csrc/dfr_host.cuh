@@ -5,6 +5,7 @@
 // call is a fixed sequence of launches (graph-capturable for plain sorts).
 #pragma once
 
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 #include <vector>
@@ -29,6 +30,10 @@ void rt_prof_begin(int kind, cudaStream_t st);
 void rt_prof_end(int kind, cudaStream_t st);
 void rt_count_launch();
 int rt_grid(const void* kern, int threads, size_t smem);
+int rt_sms();
+// The launch plan for a call of `key_type` whose arrays hold `mean_keys` keys
+// on average (the tuning table; dfr_api.cu).
+dfr_tune_t rt_tune(int key_type, uint64_t mean_keys);
 
 enum ProfKind { PK_INIT = 0, PK_ROOT_COUNT, PK_ROOT_CLASSIFY, PK_LEVEL_COUNT, PK_SCATTER, PK_CLASSIFY, PK_CTASORT,
                 PK_COPY, PK_H2D, PK_WARPSORT };
@@ -71,7 +76,9 @@ Layout make_layout(uint64_t ntot, uint32_t narr) {
   l.segcap = (uint32_t)(ntot / (TCTA + 1) + narr + 1);
   l.tilecap = (uint32_t)(ntot / TILE + l.segcap + 1);
   constexpr uint64_t WCAP = 32ull * C::WKPT;
-  l.ctacap = (uint32_t)(ntot / (WCAP + 1) + narr + 1);   // buckets of more than WCAP keys
+  // runs of more than the smallest allowed warp-sort limit (DFR_TUNE_WARP_MIN)
+  l.ctacap = (uint32_t)(ntot / (DFR_TUNE_WARP_MIN + 1) + narr + 1);
+  static_assert(DFR_TUNE_WARP_MIN <= WCAP, "warp-sort limits");
   l.wqcap = (uint32_t)(ntot / (T_WARP + 1) + narr + 1);  // buckets of more than T_WARP keys
   l.copycap = (uint32_t)(ntot / (TCTA + 1) + 1);
   l.copytilecap = (uint32_t)(ntot / TILE + l.copycap + 1);
@@ -182,6 +189,27 @@ struct Grids {
   int rc, rcl, lc, sc, cl, cs, ws, cp;
 };
 
+// The tuning entry's CTAs-per-SM caps applied to the persistent grids.
+inline void apply_tune(const dfr_tune_t& t, int sms, Grids* g) {
+  if (t.scatter_ctas_per_sm && sms > 0) g->sc = std::min(g->sc, (int)t.scatter_ctas_per_sm * sms);
+  if (t.ctasort_ctas_per_sm && sms > 0) g->cs = std::min(g->cs, (int)t.ctasort_ctas_per_sm * sms);
+}
+
+// Fill the launch-plan fields of a context from a tuning entry.
+template <class K, class V>
+void ctx_plan(Ctx* c, const dfr_tune_t& t) {
+  constexpr uint32_t WCAP = 32u * Cfg<K, V>::WKPT;
+  c->target = 1u << t.target_log2;
+  c->max_bits = t.max_bits;
+  c->warp_max = std::min(t.warp_max, WCAP);
+}
+
+template <class K, class V>
+constexpr int key_type_of() {
+  return std::is_same<V, NoVal>::value ? (sizeof(K) == 8 ? DFR_U64 : DFR_U32)
+                                       : (sizeof(K) == 8 ? DFR_U64_KV : DFR_U32_KV);
+}
+
 template <class K, class V>
 struct Kernels {
   using C = Cfg<K, V>;
@@ -269,9 +297,12 @@ int run_sort(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws
   c.spin_limit = rt_spin_limit();
   c.force_timeout = rt_force_timeout() ? 1u : 0u;
   c.nlev = (uint32_t)T::nlev;
+  const dfr_tune_t tune = rt_tune(key_type_of<K, V>(), ntot / narr);
+  ctx_plan<K, V>(&c, tune);
 
   Grids g;
   if (!T::grids([](const void* k, int t, size_t sm) { return rt_grid(k, t, sm); }, &g)) return DFR_ERR_CUDA;
+  apply_tune(tune, rt_sms(), &g);
 
   std::vector<ArrDesc> tab(narr);
   uint32_t rt = 0;

@@ -45,6 +45,7 @@ struct NoAllocDevice {
   int status;
   unsigned char* base;  // device address of g_noalloc_scratch on this device
   Grids grids;
+  int sms;
 };
 
 constexpr int kMaxDevices = 64;
@@ -74,6 +75,7 @@ int setup(int dev, NoAllocDevice* d) {
     return (per_sm < 1 ? 1 : per_sm) * sms;
   };
   if (!T::grids(grid_of, &d->grids)) return DFR_ERR_CUDA;
+  d->sms = sms;
   d->base = static_cast<unsigned char*>(p);
   return DFR_OK;
 }
@@ -109,9 +111,13 @@ extern "C" int dfr_sort_u32_noalloc(uint32_t* keys, uint64_t n, dfr_stream_t str
   c.spin_limit = rt_spin_limit();
   c.force_timeout = 0u;
   c.nlev = (uint32_t)T::nlev;
+  const dfr_tune_t tune = rt_tune(DFR_U32, n);
+  ctx_plan<K, V>(&c, tune);
+  Grids g = d->grids;
+  apply_tune(tune, d->sms, &g);
   const uint32_t rt = (uint32_t)((n + T::TILE - 1) / T::TILE);
   const ArrDesc a0{keys, buf, nullptr, nullptr, (uint32_t)n, 0u};
-  enqueue_sort<K, V>(c, lay, d->grids, 1u, rt, (unsigned long long)n, a0, true, st,
+  enqueue_sort<K, V>(c, lay, g, 1u, rt, (unsigned long long)n, a0, true, st,
                      [](int, cudaStream_t, auto&& fn) {
                        fn();
                        rt_count_launch();

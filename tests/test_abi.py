@@ -108,3 +108,45 @@ def test_server_host_checks(lib):
     assert lib.dfr_server_stats(None, None, None, None) == dfr.DFR_ERR_INVALID_ARG
     assert lib.dfr_server_destroy(None) == dfr.DFR_ERR_INVALID_ARG
     assert lib.dfr_server_set_limits(None, 1, 1) == dfr.DFR_ERR_INVALID_ARG
+
+
+def test_tune_table_api(lib):
+    """Size classes, the built-in table, overrides and their validation (no CUDA call)."""
+    assert [dfr.dfr_tune_class(n) for n in (0, 1, 4095, 4096, 16383, 16384, 1 << 20, (1 << 28) - 1, 1 << 28,
+                                            1 << 40)] == [0, 0, 0, 1, 1, 2, 5, 8, 9, 9]
+    for kt in (dfr.DFR_U32, dfr.DFR_U64, dfr.DFR_U64_KV, dfr.DFR_U32_KV):
+        for c in range(dfr.DFR_TUNE_CLASSES):
+            t = dfr.dfr_tune_get(kt, c)
+            assert 6 <= t["target_log2"] <= 13 and 4 <= t["max_bits"] <= 8
+            assert dfr.DFR_TUNE_WARP_MIN <= t["warp_max"] <= dfr.DFR_TUNE_WARP_MAX
+    base = dfr.dfr_tune_get(dfr.DFR_U32, 3)
+    try:
+        new = dict(base, target_log2=9, max_bits=6, warp_max=256, scatter_ctas_per_sm=1, ctasort_ctas_per_sm=1)
+        assert dfr.dfr_tune_set(dfr.DFR_U32, 3, new) == dfr.DFR_OK
+        assert dfr.dfr_tune_get(dfr.DFR_U32, 3) == new
+        for bad in (dict(base, target_log2=5), dict(base, target_log2=14), dict(base, max_bits=3),
+                    dict(base, max_bits=9), dict(base, warp_max=64), dict(base, warp_max=1024),
+                    dict(base, scatter_ctas_per_sm=5)):
+            assert dfr.dfr_tune_set(dfr.DFR_U32, 3, bad) == dfr.DFR_ERR_INVALID_ARG
+        assert dfr.dfr_tune_set(7, 3, base) == dfr.DFR_ERR_INVALID_ARG
+        assert dfr.dfr_tune_set(dfr.DFR_U32, dfr.DFR_TUNE_CLASSES, base) == dfr.DFR_ERR_INVALID_ARG
+    finally:
+        assert dfr.dfr_tune_reset() == dfr.DFR_OK
+    assert dfr.dfr_tune_get(dfr.DFR_U32, 3) == base
+
+
+def test_tuner_writes_a_table_the_library_compiles(tmp_path):
+    """tune.write_inc emits the 4 x DFR_TUNE_CLASSES rows the built-in table
+    expects (the checked-in table is such a file)."""
+    from paper_2207_14334_gb300 import tune
+
+    table = {"DFR_U32": {"3": dict(target_log2=11, max_bits=7, warp_max=256, scatter_ctas_per_sm=2,
+                                   ctasort_ctas_per_sm=1)}}
+    p = tmp_path / "t.inc"
+    tune.write_inc(table, path=str(p), note="test")
+    body = "".join(l for l in p.read_text().splitlines(True) if not l.startswith("//"))
+    assert body.count("{0, 0, 0}") == 4 * dfr.DFR_TUNE_CLASSES
+    assert "{11, 7, 256, 2, 1, {0, 0, 0}}" in body
+    shipped = open(tune.INC).read()
+    assert "".join(l for l in shipped.splitlines(True) if not l.startswith("//")).count("{0, 0, 0}") == \
+        4 * dfr.DFR_TUNE_CLASSES
