@@ -45,8 +45,8 @@ import synth  # noqa: E402
 # key dealt), from profiles/k_scatter_u32_uniform_2^26.md; valid only for u32
 # key-only workloads while the kernel sources hash to SCATTER_SRC_SHA (else
 # the roofline's traffic is reported as null).
-SCATTER_NCU_BYTES_PER_KEY = 7.265
-SCATTER_SRC_SHA = "ddf62fa8f16f7edf"
+SCATTER_NCU_BYTES_PER_KEY = 7.449
+SCATTER_SRC_SHA = "ab81f965c31fe026"
 
 WORKLOADS = {
     "plain_u32_2^28": dict(kind="plain", key="u32", n=1 << 28, dists=list(synth.U32_DISTRIBUTIONS)),
@@ -812,6 +812,26 @@ def main():
                 "frac": achieved / peak, "traffic": traffic, "kernel": "k_scatter",
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": scatter_bytes / max(1, scatter_launches)}
+    # Small arrays: the same sorts launched as one captured CUDA graph each
+    # (dfr_graph_*), which replaces the call's kernel launches by one.
+    graph_ms = {}
+    if n <= (1 << 22):
+        g = dfr.dfr_graph_create([(kt, work, vals if kv else 0, sorter.kbuf, sorter.vbuf if kv else 0, n)], sorter.ws,
+                                 sorter.ws_bytes)
+        try:
+            for d in inputs:
+                ts = []
+                for _ in range(max(3, args.steps)):
+                    restore(d)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    dfr.check(dfr.dfr_graph_launch(g, stream), "graph")
+                    e1.record(stream)
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                graph_ms[d] = statistics.median(ts)
+        finally:
+            dfr.dfr_graph_destroy(g)
     per_dist = {}
     for d in inputs:
         t = statistics.median(per_dist_ms[d])
@@ -823,6 +843,9 @@ def main():
                        "const_keys": p["const_keys"], "group_buckets": p["group_buckets"],
                        "cta_buckets": p["cta_buckets"], "wsort_buckets": p["wsort_buckets"],
                        "kernel_ms": prof_by_dist[d]}
+        if d in graph_ms:
+            per_dist[d]["graph_ms"] = graph_ms[d]
+            per_dist[d]["graph_gkeys_s"] = n / (graph_ms[d] * 1e-3) / 1e9
     kernel_share = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}
 
     # End to end through the C ABI: pinned host keys -> device -> sort -> host.

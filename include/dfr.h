@@ -197,6 +197,25 @@ int dfr_batch_workspace_bytes(const dfr_segment_t* segs, uint32_t count, size_t*
 int dfr_sort_batch(const dfr_segment_t* segs, uint32_t count, void* ws, size_t ws_bytes,
                    dfr_stream_t stream);
 
+/* --------------------------------------------------------------- graphs -- */
+
+/*
+ * A sort captured once into a CUDA graph and launched many times: for
+ * callers that sort the same buffers repeatedly (refilling the keys between
+ * launches), one graph launch replaces the call's ~24 kernel launches.  The
+ * graph is bound to the segments' pointers and lengths and to `ws` (which it
+ * owns while it lives: no other call may use that workspace), and to the
+ * launch plan in force at creation.  dfr_graph_create uploads the descriptor
+ * table synchronously and captures on a private stream; it fails like
+ * dfr_sort_batch on bad arguments (DFR_ERR_INVALID_ARG, DFR_ERR_WORKSPACE) or
+ * with DFR_ERR_CUDA.  dfr_graph_launch enqueues one complete sort on
+ * `stream`; device errors land in `ws` as for the other calls.
+ */
+typedef struct dfr_graph dfr_graph_t;
+int dfr_graph_create(dfr_graph_t** graph, const dfr_segment_t* segs, uint32_t count, void* ws, size_t ws_bytes);
+int dfr_graph_launch(dfr_graph_t* graph, dfr_stream_t stream);
+int dfr_graph_destroy(dfr_graph_t* graph);
+
 /* --------------------------------------------------------------- served -- */
 
 /*

@@ -102,6 +102,9 @@ _SIGNATURES = {
     "dfr_wait": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(ctypes.c_double)]),
     "dfr_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "dfr_server_destroy": (ctypes.c_int, [_vp]),
+    "dfr_graph_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(dfr_segment_t), _u32, _vp, _sz]),
+    "dfr_graph_launch": (ctypes.c_int, [_vp, _vp]),
+    "dfr_graph_destroy": (ctypes.c_int, [_vp]),
     "dfr_tune_class": (ctypes.c_int, [_u64]),
     "dfr_tune_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(dfr_tune_t)]),
     "dfr_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(dfr_tune_t)]),
@@ -303,6 +306,23 @@ def dfr_server_stats(server: int) -> dict:
 
 def dfr_server_destroy(server: int) -> int:
     return load().dfr_server_destroy(_vp(server))
+
+
+def dfr_graph_create(segs, ws, ws_bytes) -> int:
+    """Capture one sort of these segments (as for dfr_sort_batch) into a CUDA
+    graph; returns the handle (an int).  Raises DfrError on failure."""
+    arr = _segments(segs)
+    h = _vp(0)
+    check(load().dfr_graph_create(ctypes.byref(h), arr, len(segs), _ptr(ws), int(ws_bytes)), "dfr_graph_create")
+    return int(h.value)
+
+
+def dfr_graph_launch(graph: int, stream=None) -> int:
+    return load().dfr_graph_launch(_vp(graph), _stream(stream))
+
+
+def dfr_graph_destroy(graph: int) -> int:
+    return load().dfr_graph_destroy(_vp(graph))
 
 
 def dfr_tune_class(mean_keys: int) -> int:

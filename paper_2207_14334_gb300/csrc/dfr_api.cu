@@ -134,6 +134,17 @@ int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, 
   }
 }
 
+int graph_typed(int key_type, const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out,
+                uint32_t* nodes) {
+  switch (key_type) {
+    case DFR_U32: return graph_u32(a, n, ws, wsb, out, nodes);
+    case DFR_U32_KV: return graph_u32_kv(a, n, ws, wsb, out, nodes);
+    case DFR_U64: return graph_u64(a, n, ws, wsb, out, nodes);
+    case DFR_U64_KV: return graph_u64_kv(a, n, ws, wsb, out, nodes);
+    default: return DFR_ERR_INVALID_ARG;
+  }
+}
+
 int ws_typed(int key_type, uint64_t ntot, uint32_t narr, size_t* bytes) {
   switch (key_type) {
     case DFR_U32: *bytes = ws_u32(ntot, narr); return DFR_OK;
@@ -257,6 +268,43 @@ int dfr_sort_batch(const dfr_segment_t* segs, uint32_t count, void* ws, size_t w
     a[i] = HostArr{segs[i].keys, segs[i].kbuf, segs[i].vals, segs[i].vbuf, segs[i].n};
   }
   return run_typed(kt, a.data(), count, true, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+struct dfr_graph {
+  cudaGraphExec_t exec;
+  uint32_t nodes;
+};
+
+int dfr_graph_create(dfr_graph_t** out, const dfr_segment_t* segs, uint32_t count, void* ws, size_t ws_bytes) {
+  if (!out) return DFR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!segs || count == 0) return DFR_ERR_INVALID_ARG;
+  const int kt = segs[0].key_type;
+  std::vector<HostArr> a(count);
+  for (uint32_t i = 0; i < count; ++i) {
+    if (segs[i].key_type != kt) return DFR_ERR_INVALID_ARG;
+    a[i] = HostArr{segs[i].keys, segs[i].kbuf, segs[i].vals, segs[i].vbuf, segs[i].n};
+  }
+  cudaGraphExec_t exec = nullptr;
+  uint32_t nodes = 0;
+  const int rc = graph_typed(kt, a.data(), count, ws, ws_bytes, &exec, &nodes);
+  if (rc != DFR_OK) return rc;
+  *out = new dfr_graph{exec, nodes};
+  return DFR_OK;
+}
+
+int dfr_graph_launch(dfr_graph_t* g, dfr_stream_t stream) {
+  if (!g || !g->exec) return DFR_ERR_INVALID_ARG;
+  if (cudaGraphLaunch(g->exec, (cudaStream_t)stream) != cudaSuccess) return DFR_ERR_CUDA;
+  for (uint32_t i = 0; i < g->nodes; ++i) rt_count_launch();
+  return DFR_OK;
+}
+
+int dfr_graph_destroy(dfr_graph_t* g) {
+  if (!g) return DFR_ERR_INVALID_ARG;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  delete g;
+  return DFR_OK;
 }
 
 int dfr_tune_class(uint64_t mean_keys) {

@@ -328,6 +328,63 @@ int run_sort(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws
   return cudaGetLastError() == cudaSuccess ? DFR_OK : DFR_ERR_CUDA;
 }
 
+// Capture one call's launch sequence into an executable CUDA graph bound to
+// these buffers and this workspace.  The descriptor table is uploaded now
+// (synchronously), so the captured sequence is kernels only.
+template <class K, class V>
+int build_graph(const HostArr* arrs, uint32_t narr, void* ws, size_t ws_bytes, cudaGraphExec_t* out,
+                uint32_t* nodes) {
+  using T = Kernels<K, V>;
+  *out = nullptr;
+  *nodes = 0;
+  if (narr == 0) return DFR_ERR_INVALID_ARG;
+  uint64_t ntot = 0;
+  int rc = check_arrays<K, V>(arrs, narr, &ntot);
+  if (rc != DFR_OK) return rc;
+  const Layout lay = make_layout<K, V>(ntot, narr);
+  if (!ws || ((uintptr_t)ws & 255u)) return DFR_ERR_INVALID_ARG;
+  if (ws_bytes < lay.total) return DFR_ERR_WORKSPACE;
+  Ctx c = make_ctx(ws, lay, narr);
+  c.spin_limit = rt_spin_limit();
+  c.force_timeout = 0u;
+  c.nlev = (uint32_t)T::nlev;
+  const dfr_tune_t tune = rt_tune(key_type_of<K, V>(), ntot / narr);
+  ctx_plan<K, V>(&c, tune);
+  Grids g;
+  if (!T::grids([](const void* k, int t, size_t sm) { return rt_grid(k, t, sm); }, &g)) return DFR_ERR_CUDA;
+  apply_tune(tune, rt_sms(), &g);
+  std::vector<ArrDesc> tab(narr);
+  uint32_t rt = 0;
+  for (uint32_t a = 0; a < narr; ++a) {
+    const HostArr& h = arrs[a];
+    tab[a] = ArrDesc{h.keys, h.buf, h.vals, h.vbuf, (uint32_t)h.n, rt};
+    if (h.n > 1) rt += (uint32_t)((h.n + T::TILE - 1) / T::TILE);
+  }
+  if (cudaMemcpy(c.arrs, tab.data(), narr * sizeof(ArrDesc), cudaMemcpyHostToDevice) != cudaSuccess)
+    return DFR_ERR_CUDA;
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return DFR_ERR_CUDA;
+  rc = DFR_OK;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    rc = DFR_ERR_CUDA;
+  } else {
+    uint32_t n = 0;
+    enqueue_sort<K, V>(c, lay, g, narr, rt, (unsigned long long)ntot, tab[0], false, cs,
+                       [&n](int, cudaStream_t, auto&& fn) {
+                         fn();
+                         ++n;
+                       });
+    if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || !graph) rc = DFR_ERR_CUDA;
+    if (rc == DFR_OK && cudaGraphInstantiate(out, graph, 0) != cudaSuccess) rc = DFR_ERR_CUDA;
+    *nodes = n;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (rc != DFR_OK) *out = nullptr;
+  return rc;
+}
+
 // Entry points instantiated per key type (dfr_u32.cu, ...).
 int run_u32(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st);
 int run_u32_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st);
@@ -337,8 +394,14 @@ size_t ws_u32(uint64_t ntot, uint32_t narr);
 size_t ws_u32_kv(uint64_t ntot, uint32_t narr);
 size_t ws_u64(uint64_t ntot, uint32_t narr);
 size_t ws_u64_kv(uint64_t ntot, uint32_t narr);
+int graph_u32(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes);
+int graph_u32_kv(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes);
+int graph_u64(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes);
+int graph_u64_kv(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes);
 // Dispatch by key type, and the device error word as a DFR status (dfr_api.cu).
 int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st);
+int graph_typed(int key_type, const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out,
+                uint32_t* nodes);
 int ws_typed(int key_type, uint64_t ntot, uint32_t narr, size_t* bytes);
 int map_device_status(uint32_t err);
 

@@ -9,4 +9,8 @@ int run_u32(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cuda
 
 size_t ws_u32(uint64_t ntot, uint32_t narr) { return workspace_bytes<uint32_t, NoVal>(ntot, narr); }
 
+int graph_u32(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes) {
+  return build_graph<uint32_t, NoVal>(a, n, ws, wsb, out, nodes);
+}
+
 }  // namespace dfr

@@ -9,4 +9,8 @@ int run_u32_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, c
 
 size_t ws_u32_kv(uint64_t ntot, uint32_t narr) { return workspace_bytes<uint32_t, uint32_t>(ntot, narr); }
 
+int graph_u32_kv(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes) {
+  return build_graph<uint32_t, uint32_t>(a, n, ws, wsb, out, nodes);
+}
+
 }  // namespace dfr

@@ -150,3 +150,16 @@ def test_tuner_writes_a_table_the_library_compiles(tmp_path):
     shipped = open(tune.INC).read()
     assert "".join(l for l in shipped.splitlines(True) if not l.startswith("//")).count("{0, 0, 0}") == \
         4 * dfr.DFR_TUNE_CLASSES
+
+
+def test_graph_host_checks(lib):
+    h = ctypes.c_void_p(0)
+    seg = dfr.dfr_segment_t(dfr.DFR_U32, 0x1000, 0, 0x2000, 0, 10)
+    assert lib.dfr_graph_create(None, ctypes.byref(seg), 1, 0x100000, 1 << 20) == dfr.DFR_ERR_INVALID_ARG
+    assert lib.dfr_graph_create(ctypes.byref(h), None, 1, 0x100000, 1 << 20) == dfr.DFR_ERR_INVALID_ARG
+    assert lib.dfr_graph_create(ctypes.byref(h), ctypes.byref(seg), 0, 0x100000, 1 << 20) == dfr.DFR_ERR_INVALID_ARG
+    assert lib.dfr_graph_create(ctypes.byref(h), ctypes.byref(seg), 1, 0x100010, 1 << 20) == dfr.DFR_ERR_INVALID_ARG
+    assert lib.dfr_graph_create(ctypes.byref(h), ctypes.byref(seg), 1, 0x100000, 16) == dfr.DFR_ERR_WORKSPACE
+    assert h.value is None
+    assert lib.dfr_graph_launch(None, None) == dfr.DFR_ERR_INVALID_ARG
+    assert lib.dfr_graph_destroy(None) == dfr.DFR_ERR_INVALID_ARG
