@@ -170,6 +170,14 @@ def reduce_max(values, world, device):
     return t.tolist()
 
 
+def job_rate(local_ms, keys_per_rank, world, device):
+    """Whole-job throughput of a weak-scaling step: every rank sorts
+    keys_per_rank keys; the step takes as long as the slowest rank.
+    Returns (max ms over ranks, Gkeys/s of the whole job)."""
+    ms = reduce_max([local_ms], world, device)[0]
+    return ms, world * keys_per_rank / (ms * 1e-3) / 1e9
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as tdist
@@ -359,8 +367,7 @@ def run_batch(args, wl, dfr, dev, world, rank):
     clk = clocks.stop()
     t_plain = timed(plain, max(1, min(args.steps, 3)))
     t_graph = timed(graph.replay, max(1, min(args.steps, 3)))
-    ms = reduce_max([statistics.mean(t_batch)], world, dev)[0]
-    value = world * total_keys / (ms * 1e-3) / 1e9
+    ms, value = job_rate(statistics.mean(t_batch), total_keys, world, dev)
     ms_plain = statistics.median(t_plain)
     ms_graph = statistics.median(t_graph)
 
@@ -385,8 +392,8 @@ def run_batch(args, wl, dfr, dev, world, rank):
             e1.record(stream)
             e1.synchronize()
             tt.append(e0.elapsed_time(e1))
-        ems = reduce_max([statistics.mean(tt)], world, dev)[0]
-        e2e = {"value": world * total_keys / (ems * 1e-3) / 1e9, "unit": "Gkeys/s",
+        ems, e2e_rate = job_rate(statistics.mean(tt), total_keys, world, dev)
+        e2e = {"value": e2e_rate, "unit": "Gkeys/s",
                "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": int(host.nbytes), "ms_per_step": ems}
 
     cpu = None
@@ -777,9 +784,8 @@ def main():
             tot += ms
         step_ms.append(tot)
     ms_step_local = sum(step_ms) / len(step_ms)
-    ms_step = reduce_max([ms_step_local], world, dev)[0]
     keys_per_step = n * len(inputs)
-    value = world * keys_per_step / (ms_step * 1e-3) / 1e9
+    ms_step, value = job_rate(ms_step_local, keys_per_step, world, dev)
 
     # Per-kernel profile of one more step (CUDA events around every launch),
     # plus the executed plan's algorithmic bytes from the device counters.
@@ -874,8 +880,8 @@ def main():
                 e1.synchronize()
                 tot += e0.elapsed_time(e1)
             e2e_ms.append(tot)
-        ms = reduce_max([sum(e2e_ms) / len(e2e_ms)], world, dev)[0]
-        e2e = {"value": world * keys_per_step / (ms * 1e-3) / 1e9, "unit": "Gkeys/s",
+        ms, e2e_rate = job_rate(sum(e2e_ms) / len(e2e_ms), keys_per_step, world, dev)
+        e2e = {"value": e2e_rate, "unit": "Gkeys/s",
                "h2d_bytes_per_step": keys_per_step * rec, "d2h_bytes_per_step": keys_per_step * rec,
                "ms_per_step": ms}
 
