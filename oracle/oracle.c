@@ -204,6 +204,83 @@ int oracle_sort_u32_kv(uint32_t* keys, uint32_t* vals, uint64_t n)
     return 0;
 }
 
+/*
+ * Key formats: the order a sort by key uses, reduced to the unsigned order of
+ * a bijective image of the key's bits (written here from the definitions of
+ * two's complement and of IEEE 754 totalOrder, independently of the GPU
+ * library).
+ *   0 unsigned  the bits as an unsigned integer (identity);
+ *   1 signed    two's complement: adding 2^(w-1) modulo 2^w, i.e. flipping
+ *               the sign bit, maps [-2^(w-1), 2^(w-1)) monotonically onto
+ *               [0, 2^w);
+ *   2 float     IEEE 754 binary32 / binary64 totalOrder: a value with the sign
+ *               bit clear orders by its magnitude bits, above every value with
+ *               the sign bit set, which order by decreasing magnitude bits --
+ *               so set the sign bit of a positive value and flip every bit of
+ *               a negative one (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN);
+ *   flag 0x100  descending: the complement reverses the order of distinct
+ *               images; equal keys keep input order (the sort stays stable).
+ */
+#define ORACLE_FMT_DESC 0x100
+
+static uint64_t fmt_encode(uint64_t x, int bits, int fmt)
+{
+    const uint64_t all = bits == 64 ? ~(uint64_t)0 : (((uint64_t)1 << bits) - 1);
+    const uint64_t sign = (uint64_t)1 << (bits - 1);
+    const int base = fmt & 0xFF;
+    if (base == 1) {
+        x = x ^ sign;
+    } else if (base == 2) {
+        if (x & sign) x = x ^ all;   /* negative: reverse the magnitude order, below every positive */
+        else x = x | sign;           /* positive: above every negative */
+    }
+    if (fmt & ORACLE_FMT_DESC) x = x ^ all;
+    return x & all;
+}
+
+static uint64_t fmt_decode(uint64_t y, int bits, int fmt)
+{
+    const uint64_t all = bits == 64 ? ~(uint64_t)0 : (((uint64_t)1 << bits) - 1);
+    const uint64_t sign = (uint64_t)1 << (bits - 1);
+    const int base = fmt & 0xFF;
+    if (fmt & ORACLE_FMT_DESC) y = y ^ all;
+    if (base == 1) {
+        y = y ^ sign;
+    } else if (base == 2) {
+        if (y & sign) y = y & ~sign; /* was positive */
+        else y = y ^ all;            /* was negative */
+    }
+    return y & all;
+}
+
+/* Sort `n` keys of key type `key_type` (0 u32, 1 u64, 2 u64 + u32 payloads,
+ * 3 u32 + u32 payloads) in key format `fmt`: map every key to its image,
+ * sort the images with the unsigned LSD sort above, map back.  Returns as
+ * the unsigned sorts; -3 for an unknown type or format. */
+int oracle_sort_format(int key_type, int fmt, void* keys, uint32_t* vals, uint64_t n)
+{
+    uint64_t i;
+    int rc;
+    const int base = fmt & 0xFF;
+    if ((fmt & ~(0xFF | ORACLE_FMT_DESC)) != 0 || base > 2) return -3;
+    if (n == 0) return 0;
+    if (keys == NULL) return -2;
+    if (key_type == 0 || key_type == 3) {
+        uint32_t* k = (uint32_t*)keys;
+        for (i = 0; i < n; ++i) k[i] = (uint32_t)fmt_encode(k[i], 32, fmt);
+        rc = key_type == 0 ? oracle_sort_u32(k, n) : oracle_sort_u32_kv(k, vals, n);
+        for (i = 0; i < n; ++i) k[i] = (uint32_t)fmt_decode(k[i], 32, fmt);
+    } else if (key_type == 1 || key_type == 2) {
+        uint64_t* k = (uint64_t*)keys;
+        for (i = 0; i < n; ++i) k[i] = fmt_encode(k[i], 64, fmt);
+        rc = key_type == 1 ? oracle_sort_u64(k, n) : oracle_sort_u64_kv(k, vals, n);
+        for (i = 0; i < n; ++i) k[i] = fmt_decode(k[i], 64, fmt);
+    } else {
+        return -3;
+    }
+    return rc;
+}
+
 /* The single counting sort of the Preliminaries on one digit, exposed so the
  * tests can pin the count/index/deal step by itself (one digit of width 8 at
  * bit position `shift`, u32 records, stable). */

@@ -54,6 +54,22 @@ for trial in range(50):
     k16 = (k32 & np.uint32(0xF00F))
     kk, vv = orc.sort_u32_kv(k16, np.arange(n, dtype=np.uint32))
     check_kv_stable(k16, kk, vv)
+for dt, kt in ((np.int32, 0), (np.int64, 1)):
+    info = np.iinfo(dt)
+    a = g.integers(info.min, info.max, 2000, dtype=dt, endpoint=True)
+    assert np.array_equal(orc.sort_format(kt, 1, a), np.sort(a))
+    assert np.array_equal(orc.sort_format(kt, 0x101, a), np.sort(a)[::-1])
+for dt, it, kt in ((np.float32, np.uint32, 0), (np.float64, np.uint64, 1)):
+    f = (g.standard_normal(2000) * 10.0 ** g.integers(-20, 20, 2000)).astype(dt)
+    assert np.array_equal(orc.sort_format(kt, 2, f), np.sort(f, kind="stable"))
+    sign = 1 << (8 * np.dtype(dt).itemsize - 1)
+    order = np.array([int(np.array([-np.inf], dtype=dt).view(it)[0]), sign | 1, sign, 0, 1,
+                      int(np.array([np.inf], dtype=dt).view(it)[0])], dtype=it)
+    assert np.array_equal(orc.sort_format(kt, 2, order[::-1].copy().view(dt)).view(it), order)
+    assert np.array_equal(orc.sort_format(kt, 0x102, order.view(dt)).view(it), order[::-1])
+a = g.integers(-4, 4, 500).astype(np.int32)
+k, v = orc.sort_format(3, 0x101, a, np.arange(500, dtype=np.uint32))
+assert v.tolist() == sorted(range(500), key=lambda i: (-a[i], i))
 print("PINS-PASS")
 """
 
@@ -73,6 +89,10 @@ MUTANTS = [
      "const uint64_t at = index[(key >> shift) & 255u]++ ; if (i + 1 < n && ksrc[i + 1] == key) { kdst[at] = key; vdst[at] = vsrc[i + 1]; continue; }"),
     ("counting_pass_u32_kv(", "vdst[at] = vsrc[i];", "vdst[at] = vsrc[n - 1 - i];"),
     ("int oracle_sort_u32_kv(", "vt = vs; vs = vd; vd = vt;", "vt = vs;"),
+    ("static uint64_t fmt_encode(", "if (x & sign) x = x ^ all;", "if (x & sign) x = x ^ sign;"),
+    ("static uint64_t fmt_encode(", "x = x ^ sign;", "x = x ^ (sign >> 1);"),
+    ("static uint64_t fmt_decode(", "if (fmt & ORACLE_FMT_DESC) y = y ^ all;", ";"),
+    ("static uint64_t fmt_decode(", "if (y & sign) y = y & ~sign;", "if (y & sign) y = y ^ all;"),
 ]
 
 

@@ -174,3 +174,81 @@ def test_empty_and_single():
     assert oracle.sort_u64(np.array([7], np.uint64)).tolist() == [7]
     k, v = oracle.sort_u64_kv(np.empty(0, np.uint64), np.empty(0, np.uint32))
     assert k.size == 0 and v.size == 0
+
+
+# ---- key formats (signed, IEEE float total order, descending), pinned to
+# numpy's sorts and to hand-written total orders
+
+FMT_SIGNED, FMT_FLOAT, FMT_DESC = 1, 2, 0x100
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+@pytest.mark.parametrize("dt,kt", [(np.int32, 0), (np.int64, 1)])
+def test_signed_matches_numpy(dt, kt):
+    g = _rng(11)
+    info = np.iinfo(dt)
+    a = g.integers(info.min, info.max, 20000, dtype=dt, endpoint=True)
+    a[:6] = [info.min, info.max, -1, 0, 1, info.min + 1]
+    got = oracle.sort_format(kt, FMT_SIGNED, a)
+    assert got.dtype == dt and np.array_equal(got, np.sort(a))
+    desc = oracle.sort_format(kt, FMT_SIGNED | FMT_DESC, a)
+    assert np.array_equal(desc, np.sort(a)[::-1])
+
+
+@pytest.mark.parametrize("dt,kt", [(np.float32, 0), (np.float64, 1)])
+def test_float_finite_matches_numpy(dt, kt):
+    g = _rng(12)
+    a = (g.standard_normal(20000) * 10.0 ** g.integers(-30, 30, 20000)).astype(dt)
+    a[:5] = [np.inf, -np.inf, np.finfo(dt).tiny / 4, -np.finfo(dt).tiny / 4, 0.0]  # with subnormals; no -0.0, no NaN
+    got = oracle.sort_format(kt, FMT_FLOAT, a)
+    assert np.array_equal(got, np.sort(a, kind="stable"))
+    assert np.array_equal(oracle.sort_format(kt, FMT_FLOAT | FMT_DESC, a), np.sort(a)[::-1])
+
+
+@pytest.mark.parametrize("dt,it,kt", [(np.float32, np.uint32, 0), (np.float64, np.uint64, 1)])
+def test_float_special_values_total_order(dt, it, kt):
+    bits = 8 * np.dtype(dt).itemsize
+    sign = 1 << (bits - 1)
+    qnan = np.array([np.nan], dtype=dt).view(it)[0]
+    order = [int(qnan) | sign | 5,  # a negative NaN with a larger payload sorts first
+             int(qnan) | sign,
+             int(np.array([-np.inf], dtype=dt).view(it)[0]),
+             int(np.array([-1.5], dtype=dt).view(it)[0]),
+             sign | 1,  # the negative subnormal closest to zero
+             sign,  # -0.0
+             0,  # +0.0
+             1,  # the smallest positive subnormal
+             int(np.array([2.0], dtype=dt).view(it)[0]),
+             int(np.array([np.inf], dtype=dt).view(it)[0]),
+             int(qnan),
+             int(qnan) | 5]
+    expected = np.array(order, dtype=it)
+    g = _rng(13)
+    shuffled = expected[g.permutation(expected.size)]
+    assert np.array_equal(oracle.sort_format(kt, FMT_FLOAT, shuffled.view(dt)).view(it), expected)
+    assert np.array_equal(oracle.sort_format(kt, FMT_FLOAT | FMT_DESC, shuffled.view(dt)).view(it), expected[::-1])
+
+
+@pytest.mark.parametrize("kt,dt", [(3, np.int32), (2, np.int64)])
+def test_formats_key_value_stability(kt, dt):
+    g = _rng(14)
+    n = 3000
+    a = g.integers(-5, 5, n).astype(dt)  # many ties
+    v = np.arange(n, dtype=np.uint32)
+    for fmt, key in ((FMT_SIGNED, lambda i: (a[i], i)), (FMT_SIGNED | FMT_DESC, lambda i: (-a[i], i))):
+        k, vv = oracle.sort_format(kt, fmt, a, v)
+        order = sorted(range(n), key=key)
+        assert np.array_equal(vv, np.array(order, dtype=np.uint32))
+        assert np.array_equal(k, a[order])
+
+
+def test_unsigned_descending_and_bad_format():
+    g = _rng(15)
+    a = g.integers(0, 1 << 32, 5000, dtype=np.uint64).astype(np.uint32)
+    assert np.array_equal(oracle.sort_format(0, FMT_DESC, a), np.sort(a)[::-1])
+    assert np.array_equal(oracle.sort_format(0, 0, a), np.sort(a))
+    with pytest.raises(RuntimeError):
+        oracle.sort_format(0, 3, a)
