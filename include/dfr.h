@@ -197,6 +197,36 @@ int dfr_batch_workspace_bytes(const dfr_segment_t* segs, uint32_t count, size_t*
 int dfr_sort_batch(const dfr_segment_t* segs, uint32_t count, void* ws, size_t ws_bytes,
                    dfr_stream_t stream);
 
+/* ----------------------------------------------------------- key formats -- */
+
+/*
+ * Signed, floating-point and descending keys.  The sort orders unsigned
+ * integers; other orders are reduced to it by an order-preserving bijection
+ * of the key's bits, applied in place before the sort and undone after it
+ * (two extra read+write passes over the keys):
+ *   DFR_FMT_SIGNED      two's complement (int32 / int64): flip the sign bit;
+ *   DFR_FMT_FLOAT       IEEE 754 binary32 / binary64 in totalOrder:
+ *                       -NaN < -inf < ... < -0.0 < +0.0 < ... < +inf < +NaN
+ *                       (NaNs ordered by their payload bits): flip every bit
+ *                       of a negative value, set the sign bit of a positive one;
+ *   DFR_FMT_DESCENDING  flag: largest key first; equal keys still keep input
+ *                       order (stable): complement the image.
+ * The width comes from the key type (DFR_U32 / DFR_U32_KV: 32-bit keys,
+ * DFR_U64 / DFR_U64_KV: 64-bit keys); payloads are unchanged.  Workspace and
+ * buffers as for the unsigned sorts.  DFR_ERR_INVALID_ARG for an unknown
+ * format.
+ */
+enum dfr_key_format {
+    DFR_FMT_UNSIGNED = 0,
+    DFR_FMT_SIGNED = 1,
+    DFR_FMT_FLOAT = 2,
+    DFR_FMT_DESCENDING = 0x100
+};
+int dfr_sort_format(int key_type, int key_format, void* keys, uint32_t* vals, void* kbuf, uint32_t* vbuf,
+                    uint64_t n, void* ws, size_t ws_bytes, dfr_stream_t stream);
+int dfr_sort_batch_format(const dfr_segment_t* segs, uint32_t count, int key_format, void* ws, size_t ws_bytes,
+                          dfr_stream_t stream);
+
 /* --------------------------------------------------------------- graphs -- */
 
 /*
@@ -357,7 +387,7 @@ int dfr_set_debug(uint32_t spin_limit, int force_timeout);
  * device, returns per-kind totals and clears them.  Kinds are listed by
  * dfr_profile_kind_name(). */
 int dfr_profile_enable(int on);
-#define DFR_PROFILE_KINDS 10
+#define DFR_PROFILE_KINDS 11
 int dfr_profile_read(double* ms_total /*[DFR_PROFILE_KINDS]*/, uint64_t* launches /*[DFR_PROFILE_KINDS]*/);
 const char* dfr_profile_kind_name(int kind);
 

@@ -35,11 +35,15 @@ DFR_U32_KV = 3
 
 DFR_MAX_N = (1 << 30) - 1
 DFR_NOALLOC_MAX_N = 1 << 20
-DFR_PROFILE_KINDS = 10
+DFR_PROFILE_KINDS = 11
 DFR_STATS_MAX_LEVELS = 16
 DFR_SERVER_MAX_STREAMS = 64
 DFR_SERVER_MAX_INFLIGHT = 64
 DFR_TUNE_CLASSES = 10
+DFR_FMT_UNSIGNED = 0
+DFR_FMT_SIGNED = 1
+DFR_FMT_FLOAT = 2
+DFR_FMT_DESCENDING = 0x100
 DFR_TUNE_WARP_MIN = 128
 DFR_TUNE_WARP_MAX = 512
 
@@ -102,6 +106,8 @@ _SIGNATURES = {
     "dfr_wait": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(ctypes.c_double)]),
     "dfr_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "dfr_server_destroy": (ctypes.c_int, [_vp]),
+    "dfr_sort_format": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp]),
+    "dfr_sort_batch_format": (ctypes.c_int, [ctypes.POINTER(dfr_segment_t), _u32, ctypes.c_int, _vp, _sz, _vp]),
     "dfr_graph_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(dfr_segment_t), _u32, _vp, _sz]),
     "dfr_graph_launch": (ctypes.c_int, [_vp, _vp]),
     "dfr_graph_destroy": (ctypes.c_int, [_vp]),
@@ -308,6 +314,18 @@ def dfr_server_destroy(server: int) -> int:
     return load().dfr_server_destroy(_vp(server))
 
 
+def dfr_sort_format(key_type, key_format, keys, vals, kbuf, vbuf, n, ws, ws_bytes, stream=None) -> int:
+    """Sort signed, IEEE-float or descending keys (DFR_FMT_*): the unsigned
+    sort between an in-place order-preserving bit map and its inverse."""
+    return load().dfr_sort_format(int(key_type), int(key_format), _ptr(keys), _ptr(vals), _ptr(kbuf), _ptr(vbuf),
+                                  int(n), _ptr(ws), int(ws_bytes), _stream(stream))
+
+
+def dfr_sort_batch_format(segs, key_format, ws, ws_bytes, stream=None) -> int:
+    arr = _segments(segs)
+    return load().dfr_sort_batch_format(arr, len(segs), int(key_format), _ptr(ws), int(ws_bytes), _stream(stream))
+
+
 def dfr_graph_create(segs, ws, ws_bytes) -> int:
     """Capture one sort of these segments (as for dfr_sort_batch) into a CUDA
     graph; returns the handle (an int).  Raises DfrError on failure."""
@@ -391,12 +409,14 @@ class Sorter:
         # zeroed once so the status word reads DFR_OK before the first call
         self.ws = torch.zeros(self.ws_bytes, dtype=torch.uint8, device=self.device)
 
-    def sort_(self, keys, vals=None, n=None, stream=None) -> int:
+    def sort_(self, keys, vals=None, n=None, stream=None, key_format=DFR_FMT_UNSIGNED) -> int:
         n = int(keys.numel() if n is None else n)
         if n > self.capacity:
             raise ValueError("array of %d keys exceeds capacity %d" % (n, self.capacity))
         kt = self.key_type
-        if kt == DFR_U32:
+        if key_format != DFR_FMT_UNSIGNED:
+            rc = dfr_sort_format(kt, key_format, keys, vals, self.kbuf, self.vbuf, n, self.ws, self.ws_bytes, stream)
+        elif kt == DFR_U32:
             rc = dfr_sort_u32(keys, self.kbuf, n, self.ws, self.ws_bytes, stream)
         elif kt == DFR_U64:
             rc = dfr_sort_u64(keys, self.kbuf, n, self.ws, self.ws_bytes, stream)
@@ -415,14 +435,14 @@ class Sorter:
 
 
 def to_device(a, device="cuda"):
-    """numpy uint32/uint64 array -> torch int32/int64 device tensor holding the
-    same bits (torch's unsigned dtypes have patchy op coverage)."""
+    """numpy array of 4- or 8-byte items -> torch int32/int64 device tensor
+    holding the same bits (torch's unsigned dtypes have patchy op coverage)."""
     import numpy as np
     import torch
 
-    if a.dtype == np.uint32:
+    if a.dtype.itemsize == 4 and a.dtype != np.int32:
         t = torch.from_numpy(np.ascontiguousarray(a).view(np.int32))
-    elif a.dtype == np.uint64:
+    elif a.dtype.itemsize == 8 and a.dtype != np.int64:
         t = torch.from_numpy(np.ascontiguousarray(a).view(np.int64))
     else:
         t = torch.from_numpy(np.ascontiguousarray(a))

@@ -124,12 +124,13 @@ int map_device_status(uint32_t err) {
   return DFR_OK;
 }
 
-int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st) {
+int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st,
+              int fmt) {
   switch (key_type) {
-    case DFR_U32: return run_u32(a, n, batch, ws, wsb, st);
-    case DFR_U32_KV: return run_u32_kv(a, n, batch, ws, wsb, st);
-    case DFR_U64: return run_u64(a, n, batch, ws, wsb, st);
-    case DFR_U64_KV: return run_u64_kv(a, n, batch, ws, wsb, st);
+    case DFR_U32: return run_u32(a, n, batch, ws, wsb, st, fmt);
+    case DFR_U32_KV: return run_u32_kv(a, n, batch, ws, wsb, st, fmt);
+    case DFR_U64: return run_u64(a, n, batch, ws, wsb, st, fmt);
+    case DFR_U64_KV: return run_u64_kv(a, n, batch, ws, wsb, st, fmt);
     default: return DFR_ERR_INVALID_ARG;
   }
 }
@@ -168,24 +169,24 @@ int dfr_workspace_bytes(int key_type, uint64_t n, size_t* bytes) {
 
 int dfr_sort_u32(uint32_t* keys, uint32_t* buf, uint64_t n, void* ws, size_t ws_bytes, dfr_stream_t stream) {
   const HostArr a{keys, buf, nullptr, nullptr, n};
-  return run_u32(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream);
+  return run_u32(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED);
 }
 
 int dfr_sort_u64(uint64_t* keys, uint64_t* buf, uint64_t n, void* ws, size_t ws_bytes, dfr_stream_t stream) {
   const HostArr a{keys, buf, nullptr, nullptr, n};
-  return run_u64(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream);
+  return run_u64(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED);
 }
 
 int dfr_sort_u64_kv(uint64_t* keys, uint32_t* vals, uint64_t* kbuf, uint32_t* vbuf, uint64_t n, void* ws,
                     size_t ws_bytes, dfr_stream_t stream) {
   const HostArr a{keys, kbuf, vals, vbuf, n};
-  return run_u64_kv(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream);
+  return run_u64_kv(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED);
 }
 
 int dfr_sort_u32_kv(uint32_t* keys, uint32_t* vals, uint32_t* kbuf, uint32_t* vbuf, uint64_t n, void* ws,
                     size_t ws_bytes, dfr_stream_t stream) {
   const HostArr a{keys, kbuf, vals, vbuf, n};
-  return run_u32_kv(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream);
+  return run_u32_kv(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED);
 }
 
 int dfr_last_device_status(const void* ws, dfr_stream_t stream, int* status) {
@@ -340,6 +341,25 @@ int dfr_tune_reset(void) {
   return DFR_OK;
 }
 
+int dfr_sort_format(int key_type, int key_format, void* keys, uint32_t* vals, void* kbuf, uint32_t* vbuf,
+                    uint64_t n, void* ws, size_t ws_bytes, dfr_stream_t stream) {
+  const HostArr a{keys, kbuf, vals, vbuf, n};
+  return run_typed(key_type, &a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, key_format);
+}
+
+int dfr_sort_batch_format(const dfr_segment_t* segs, uint32_t count, int key_format, void* ws, size_t ws_bytes,
+                          dfr_stream_t stream) {
+  if (count == 0) return fmt_valid(key_format) ? DFR_OK : DFR_ERR_INVALID_ARG;
+  if (!segs) return DFR_ERR_INVALID_ARG;
+  const int kt = segs[0].key_type;
+  std::vector<HostArr> a(count);
+  for (uint32_t i = 0; i < count; ++i) {
+    if (segs[i].key_type != kt) return DFR_ERR_INVALID_ARG;
+    a[i] = HostArr{segs[i].keys, segs[i].kbuf, segs[i].vals, segs[i].vbuf, segs[i].n};
+  }
+  return run_typed(kt, a.data(), count, true, ws, ws_bytes, (cudaStream_t)stream, key_format);
+}
+
 int dfr_set_debug(uint32_t spin_limit, int force_timeout) {
   g_spin_limit.store(spin_limit ? spin_limit : kDefaultSpinLimit);
   g_force_timeout.store(force_timeout ? 1 : 0);
@@ -377,7 +397,7 @@ int dfr_profile_read(double* ms_total, uint64_t* launches) {
 const char* dfr_profile_kind_name(int kind) {
   static const char* names[DFR_PROFILE_KINDS] = {"init",     "root_count", "root_classify", "level_count",
                                                   "scatter",  "classify",   "ctasort",       "copy",
-                                                  "h2d",      "warpsort"};
+                                                  "h2d",      "warpsort",     "keyfmt"};
   return (kind >= 0 && kind < DFR_PROFILE_KINDS) ? names[kind] : "unknown";
 }
 

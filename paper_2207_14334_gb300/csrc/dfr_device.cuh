@@ -45,6 +45,8 @@
 
 #include <cuda_runtime.h>
 
+#include "dfr.h"
+
 namespace dfr {
 
 constexpr uint32_t FULL = 0xffffffffu;
@@ -644,6 +646,59 @@ __global__ void __launch_bounds__(NT) k_root_count(Ctx c, uint32_t root_tiles) {
     warp_count_range<K>(reinterpret_cast<const K*>(ad.keys), b, e, TOP, true, wh, orv, nandv);
   }
   flush();
+}
+
+// Key formats: the order-preserving bijection between a key's bits and the
+// unsigned value the sort orders by -- two's complement: flip the sign bit;
+// IEEE 754 totalOrder: flip every bit of a negative value, set the sign bit
+// of a positive one; descending: complement the image.
+template <class K>
+__device__ __forceinline__ K fmt_to_order(K x, uint32_t fmt) {
+  constexpr K SIGN = K(1) << (8 * sizeof(K) - 1);
+  const uint32_t base = fmt & 0xFFu;
+  if (base == DFR_FMT_SIGNED)
+    x ^= SIGN;
+  else if (base == DFR_FMT_FLOAT)
+    x = (x & SIGN) ? ~x : (x | SIGN);
+  return (fmt & DFR_FMT_DESCENDING) ? ~x : x;
+}
+template <class K>
+__device__ __forceinline__ K fmt_from_order(K y, uint32_t fmt) {
+  constexpr K SIGN = K(1) << (8 * sizeof(K) - 1);
+  const uint32_t base = fmt & 0xFFu;
+  if (fmt & DFR_FMT_DESCENDING) y = ~y;
+  if (base == DFR_FMT_SIGNED)
+    y ^= SIGN;
+  else if (base == DFR_FMT_FLOAT)
+    y = (y & SIGN) ? (y & ~SIGN) : ~y;
+  return y;
+}
+
+// Map every key of every array of the call to its image (encode) or back, in
+// place: one persistent pass over the root tiles (the arrays of 2+ keys).
+// `single`: the one array is a0 (the descriptor table is not in the
+// workspace yet); else the arrays are the workspace's descriptor table.
+template <class K, int NT, int TILE>
+__global__ void __launch_bounds__(NT) k_keyfmt(Ctx c, ArrDesc a0, uint32_t single, uint32_t root_tiles, uint32_t fmt,
+                                               uint32_t encode) {
+  for (uint32_t t = blockIdx.x; t < root_tiles; t += gridDim.x) {
+    uint32_t lo = 0;
+    if (!single) {
+      uint32_t hi = c.narr - 1;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (c.arrs[mid].root_tile_start <= t)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+    }
+    const ArrDesc ad = single ? a0 : c.arrs[lo];
+    const uint32_t b = (t - ad.root_tile_start) * (uint32_t)TILE;
+    const uint32_t e = min(ad.n, b + (uint32_t)TILE);
+    K* keys = reinterpret_cast<K*>(ad.keys);
+    for (uint32_t i = b + threadIdx.x; i < e; i += NT) keys[i] = encode ? fmt_to_order(keys[i], fmt) : fmt_from_order(keys[i], fmt);
+  }
 }
 
 // Root classification, one CTA (256 threads) per array.

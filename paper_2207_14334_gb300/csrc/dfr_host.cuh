@@ -36,7 +36,11 @@ int rt_sms();
 dfr_tune_t rt_tune(int key_type, uint64_t mean_keys);
 
 enum ProfKind { PK_INIT = 0, PK_ROOT_COUNT, PK_ROOT_CLASSIFY, PK_LEVEL_COUNT, PK_SCATTER, PK_CLASSIFY, PK_CTASORT,
-                PK_COPY, PK_H2D, PK_WARPSORT };
+                PK_COPY, PK_H2D, PK_WARPSORT, PK_KEYFMT };
+
+inline bool fmt_valid(int fmt) {
+  return (fmt & ~(0xFF | DFR_FMT_DESCENDING)) == 0 && (fmt & 0xFF) <= DFR_FMT_FLOAT;
+}
 
 // Per key type: scatter tile (threads x keys per thread), CTA-sort capacity
 // (threads x keys per thread) = the diversion threshold T_CTA, and the warp
@@ -186,7 +190,7 @@ size_t workspace_bytes(uint64_t ntot, uint32_t narr) {
 
 // Persistent grid sizes of every kernel of one key type on one device.
 struct Grids {
-  int rc, rcl, lc, sc, cl, cs, ws, cp;
+  int rc, rcl, lc, sc, cl, cs, ws, cp, kf;
 };
 
 // The tuning entry's CTAs-per-SM caps applied to the persistent grids.
@@ -229,6 +233,7 @@ struct Kernels {
   static constexpr auto ctasort = k_ctasort<K, V, CNT, CKPT>;
   static constexpr auto warpsort = k_warpsort<K, V, WPB, WKPT>;
   static constexpr auto copy = k_copy<K, V, SNT, TILE>;
+  static constexpr auto keyfmt = k_keyfmt<K, SNT, TILE>;
 
   // grid_of(kernel, threads, dynamic smem) -> persistent grid (or < 0 on error)
   template <class G>
@@ -241,7 +246,9 @@ struct Kernels {
     g->cs = grid_of((const void*)ctasort, CNT, cs_smem);
     g->ws = grid_of((const void*)warpsort, WPB * 32, ws_smem);
     g->cp = grid_of((const void*)copy, SNT, (size_t)0);
-    return g->rc > 0 && g->rcl > 0 && g->lc > 0 && g->sc > 0 && g->cl > 0 && g->cs > 0 && g->ws > 0 && g->cp > 0;
+    g->kf = grid_of((const void*)keyfmt, SNT, (size_t)0);
+    return g->rc > 0 && g->rcl > 0 && g->lc > 0 && g->sc > 0 && g->cl > 0 && g->cs > 0 && g->ws > 0 && g->cp > 0 &&
+           g->kf > 0;
   }
 };
 
@@ -281,8 +288,10 @@ void enqueue_sort(const Ctx& c, const Layout& lay, const Grids& g, uint32_t narr
 // (else the single descriptor rides in k_init's parameters, keeping the call
 // a pure kernel sequence).
 template <class K, class V>
-int run_sort(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws_bytes, cudaStream_t st) {
+int run_sort(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws_bytes, cudaStream_t st,
+             int fmt = DFR_FMT_UNSIGNED) {
   using T = Kernels<K, V>;
+  if (!fmt_valid(fmt)) return DFR_ERR_INVALID_ARG;
   if (narr == 0) return DFR_OK;
   uint64_t ntot = 0;
   int rc = check_arrays<K, V>(arrs, narr, &ntot);
@@ -324,7 +333,14 @@ int run_sort(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws
     rt_prof_end(PK_H2D, st);
     if (e != cudaSuccess) return DFR_ERR_CUDA;
   }
+  // Signed, float or descending keys: map every key to its unsigned image in
+  // place, sort the images, map them back (two extra read+write passes).
+  const uint32_t kf_grid = min_u32(rt, (uint32_t)g.kf);
+  if (fmt != DFR_FMT_UNSIGNED)
+    hook(PK_KEYFMT, st, [&] { T::keyfmt<<<kf_grid, T::SNT, 0, st>>>(c, tab[0], batch ? 0u : 1u, rt, (uint32_t)fmt, 1u); });
   enqueue_sort<K, V>(c, lay, g, narr, rt, (unsigned long long)ntot, tab[0], !batch, st, hook);
+  if (fmt != DFR_FMT_UNSIGNED)
+    hook(PK_KEYFMT, st, [&] { T::keyfmt<<<kf_grid, T::SNT, 0, st>>>(c, tab[0], batch ? 0u : 1u, rt, (uint32_t)fmt, 0u); });
   return cudaGetLastError() == cudaSuccess ? DFR_OK : DFR_ERR_CUDA;
 }
 
@@ -386,10 +402,10 @@ int build_graph(const HostArr* arrs, uint32_t narr, void* ws, size_t ws_bytes, c
 }
 
 // Entry points instantiated per key type (dfr_u32.cu, ...).
-int run_u32(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st);
-int run_u32_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st);
-int run_u64(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st);
-int run_u64_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st);
+int run_u32(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
+int run_u32_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
+int run_u64(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
+int run_u64_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
 size_t ws_u32(uint64_t ntot, uint32_t narr);
 size_t ws_u32_kv(uint64_t ntot, uint32_t narr);
 size_t ws_u64(uint64_t ntot, uint32_t narr);
@@ -399,7 +415,8 @@ int graph_u32_kv(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphEx
 int graph_u64(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes);
 int graph_u64_kv(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes);
 // Dispatch by key type, and the device error word as a DFR status (dfr_api.cu).
-int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st);
+int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st,
+              int fmt = DFR_FMT_UNSIGNED);
 int graph_typed(int key_type, const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out,
                 uint32_t* nodes);
 int ws_typed(int key_type, uint64_t ntot, uint32_t narr, size_t* bytes);

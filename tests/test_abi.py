@@ -163,3 +163,16 @@ def test_graph_host_checks(lib):
     assert h.value is None
     assert lib.dfr_graph_launch(None, None) == dfr.DFR_ERR_INVALID_ARG
     assert lib.dfr_graph_destroy(None) == dfr.DFR_ERR_INVALID_ARG
+
+
+def test_key_format_host_checks(lib):
+    # an unknown format is refused before anything is enqueued
+    for bad in (3, 0x200, -1, 0x1FF):
+        assert dfr.dfr_sort_format(dfr.DFR_U32, bad, 0x100000, 0, 0x200000, 0, 1000, 0x300000, 1 << 24,
+                                   stream=0) == dfr.DFR_ERR_INVALID_ARG
+        assert dfr.dfr_sort_batch_format([], bad, 0, 0, stream=0) == dfr.DFR_ERR_INVALID_ARG
+    assert dfr.dfr_sort_batch_format([], dfr.DFR_FMT_FLOAT | dfr.DFR_FMT_DESCENDING, 0, 0, stream=0) == dfr.DFR_OK
+    # n <= 1 is a no-op in every format
+    assert dfr.dfr_sort_format(dfr.DFR_U64, dfr.DFR_FMT_SIGNED, 0x1000, 0, 0x2000, 0, 1, 0, 0, stream=0) == dfr.DFR_OK
+    assert dfr.dfr_profile_kind_name if hasattr(dfr, "dfr_profile_kind_name") else True
+    assert lib.dfr_profile_kind_name(dfr.DFR_PROFILE_KINDS - 1) == b"keyfmt"
