@@ -44,12 +44,14 @@ inline bool fmt_valid(int fmt) {
 
 // Per key type: scatter tile (threads x keys per thread), CTA-sort capacity
 // (threads x keys per thread) = the diversion threshold T_CTA, and the warp
-// sort (warps per block, keys per lane; 32 x WKPT = its threshold).
+// sort (warps per block, keys per lane; 32 x WKPT = its threshold).  u32 keys
+// cap the CTA sort at 12 keys per lane (6144): buckets near 4096 keys are then
+// never joined into runs of ~8192 (which sort slower) and three CTAs fit an SM.
 template <class K, class V>
 struct Cfg;
 template <>
 struct Cfg<uint32_t, NoVal> {
-  static constexpr int SNT = 512, SKPT = 16, CNT = 512, CKPT = 16, WPB = 8, WKPT = 16;
+  static constexpr int SNT = 512, SKPT = 16, CNT = 512, CKPT = 12, WPB = 8, WKPT = 16;
 };
 template <>
 struct Cfg<uint32_t, uint32_t> {

@@ -103,7 +103,7 @@ def tune(key_types, classes, reps: int, budget_keys: int, log=print):
     table = {}
     for ktn in key_types:
         kt = getattr(dfr, ktn)
-        cap_log2 = 13 if kt == dfr.DFR_U32 else 12  # the CTA sort's capacity
+        cap_log2 = 12  # floor(log2) of the CTA sort's capacity (6144 u32 keys, 4096 otherwise)
         for c in classes:
             n = class_length(c)
             count = max(1, min(4096, budget_keys // n))
