@@ -1284,10 +1284,28 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
       const uint32_t nr = s_nrun;
       // run classes: single key, tiny (warp sort here), warp-sort queue, CTA queue
       uint32_t rcls = 0, rloc = 0, rlen = 0, roff = 0;
+      bool rcopy = false;
       if (threadIdx.x < nr) {
         roff = s_run_off[threadIdx.x];
         rlen = s_run_len[threadIdx.x];
-        if (rlen == 1u) {
+        if (seg.shift == 0u) {
+          // The window reached bit 0: every bucket of the run holds one
+          // repeated key (§MSD).  The run is final where it lies, or only
+          // moves back from the buffer: the tiny pass copies up to a warp of
+          // keys, a CTA-queue copy item the rest.
+          atomicAdd(&s_stat[0], 1ull);
+          atomicAdd(&s_stat[1], (unsigned long long)rlen);
+          if (pout) {
+            atomicAdd(&s_stat[2], (unsigned long long)rlen);
+            if (rlen <= T_WARP) {
+              rcls = 1;
+            } else {
+              rcls = 4;
+              rcopy = true;
+              rloc = atomicAdd(&s_qn[1], 1u);
+            }
+          }
+        } else if (rlen == 1u) {
           atomicAdd(&s_stat[0], 1ull);
           atomicAdd(&s_stat[1], 1ull);
           if (pout) {
@@ -1324,7 +1342,7 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
       if (rcls >= 3) {
         const uint32_t q = s_qbase[rcls - 3] + rloc;
         if (q < (rcls == 3 ? c.wqcap : c.ctacap))
-          (rcls == 3 ? c.w_q : c.cta_q)[q] = Item{roff, rlen, seg.arr, pout};
+          (rcls == 3 ? c.w_q : c.cta_q)[q] = Item{roff, rlen, seg.arr, pout | (rcopy ? ITEM_COPY : 0u)};
         else
           atomicOr(&ctl->err, DERR_CAPACITY);
       }
