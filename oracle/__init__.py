@@ -7,8 +7,11 @@ and the CUDA path never falls back to it.
 The arithmetic lives in ``oracle.c``: a plain least-significant-digit radix
 sort made of counting sorts (8-bit digits, every pass run, stable), following
 the paper's Preliminaries (count / convert counts to indices / deal) and its
-LSD radix sort (Algorithm 1).  This module only compiles that file with gcc
-and marshals numpy arrays to it.
+LSD radix sort (Algorithm 1), and the estimated deal of Fast Radix played
+out record by record (Algorithm 3: how many records overflow buckets of a
+given estimated size).  This module compiles that file with gcc and marshals
+numpy arrays to it; it also holds the paper's overflow model (Section
+"Analysis", Eq. 1-2) in fp64 numpy, written out as a plain sum.
 """
 from __future__ import annotations
 
@@ -47,6 +50,7 @@ def load_library(path: str):
         ("oracle_sort_u32_kv", [p, p, u64]),
         ("oracle_counting_pass_u32", [p, p, u64, ctypes.c_int]),
         ("oracle_sort_format", [ctypes.c_int, ctypes.c_int, p, p, u64]),
+        ("oracle_overflow_count", [p, u64, ctypes.c_int, ctypes.c_int, u64, p]),
     ):
         fn = getattr(lib, name)
         fn.argtypes = args
@@ -122,6 +126,18 @@ class Oracle:
                                            k.size))
         return k if v is None else (k, v)
 
+    def overflow_count(self, keys, shift: int, cap: int) -> int:
+        """Records that overflow when `keys` (u32 or u64) are dealt on the 8-bit
+        digit at `shift` into 256 estimated buckets of `cap` records each
+        (Fast Radix's estimated deal, Algorithm 3)."""
+        k = np.ascontiguousarray(keys)
+        if k.dtype not in (np.uint32, np.uint64):
+            raise ValueError("u32 or u64 keys")
+        out = ctypes.c_uint64(0)
+        _check(self.lib.oracle_overflow_count(_ptr(k), k.size, k.dtype.itemsize, int(shift), int(cap),
+                                              ctypes.byref(out)))
+        return int(out.value)
+
     def counting_pass_u32(self, keys, shift: int) -> np.ndarray:
         src = np.array(keys, dtype=np.uint32, copy=True, order="C")
         dst = np.empty_like(src)
@@ -161,3 +177,50 @@ def sort_format(key_type, fmt, keys, vals=None):
 
 def counting_pass_u32(keys, shift: int):
     return default().counting_pass_u32(keys, shift)
+
+
+def overflow_count(keys, shift: int, cap: int) -> int:
+    return default().overflow_count(keys, shift, cap)
+
+
+# ----------------------------------------------------------- overflow model --
+#
+# Section "Analysis", Eq. 1-2: for N uniformly distributed records dealt into
+# M buckets whose size is estimated as N/M, the fraction of records that
+# overflow their estimate.  Eq. 2 defines, for k = 0, 1, ..., the term
+#     g_o(N, M, k) = (N/M - k) * (M/N) * C(N, k) (1/M)^k (1 - 1/M)^(N-k),
+# i.e. (M/N) times the shortfall below N/M of a bucket that received exactly
+# k records, weighted by the binomial probability of that.  Eq. 1 (printed
+# garbled: its right-hand side uses the three-argument g_o) relates
+# consecutive N.  Reading taken here: the two-argument g_o(N, M) is the sum of
+# the Eq. 2 terms over the buckets that fall short, k = 0 .. ceil(N/M) - 1.
+# Every bucket's shortfall below the mean equals in expectation its excess
+# above the mean, so this is the expected overflow fraction for a real-valued
+# estimate N/M; when M divides N it is exactly the expected fraction of
+# records that overflow buckets of N/M records.  The reading reproduces Eq. 1
+# exactly (the tests check the recursion), which the ceiling/floor
+# alternatives do not.
+
+def overflow_term(N: int, M: int, k: int) -> float:
+    """One term g_o(N, M, k) of Eq. 2, in fp64."""
+    from scipy.special import gammaln
+
+    if k < 0 or k > N:
+        return 0.0
+    lp = (gammaln(N + 1) - gammaln(k + 1) - gammaln(N - k + 1) + k * np.log(1.0 / M)
+          + (N - k) * np.log1p(-1.0 / M))
+    return float((N / M - k) * (M / N) * np.exp(lp))
+
+
+def overflow_fraction(N: int, M: int) -> float:
+    """g_o(N, M): the sum of the Eq. 2 terms over k = 0 .. ceil(N/M) - 1, in
+    fp64 (binomial probabilities through log-gamma)."""
+    from scipy.special import gammaln
+
+    if N <= 0 or M <= 0:
+        raise ValueError("N and M must be positive")
+    kmax = -(-N // M)
+    k = np.arange(kmax, dtype=np.float64)
+    lp = (gammaln(N + 1) - gammaln(k + 1) - gammaln(N - k + 1) + k * np.log(1.0 / M)
+          + (N - k) * np.log1p(-1.0 / M))
+    return float(np.sum((N / M - k) * (M / N) * np.exp(lp)))

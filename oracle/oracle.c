@@ -302,3 +302,34 @@ int oracle_counting_pass_u32(const uint32_t* src, uint32_t* dst, uint64_t n, int
     }
     return 0;
 }
+
+/*
+ * The estimated deal of Fast Radix (Section "Diverting Fast Radix",
+ * Algorithm 3): records are dealt on one 8-bit digit into M = 256 buckets
+ * whose sizes are not counted but estimated, each bucket holding `cap`
+ * records; a record that finds its bucket full goes to the overflow region
+ * instead.  This function plays that deal out record by record, in input
+ * order, and returns in *out how many records went to the overflow region.
+ * (Keys of `width` 4 or 8 bytes; digit = (key >> shift) & 255.)
+ * Returns -2 on a bad argument.
+ */
+int oracle_overflow_count(const void* keys, uint64_t n, int width, int shift, uint64_t cap, uint64_t* out)
+{
+    uint64_t fill[ORACLE_BUCKETS];
+    uint64_t over = 0;
+    uint64_t i;
+    int d;
+    if (out == NULL || (width != 4 && width != 8) || shift < 0 || shift > 8 * width - 8) return -2;
+    if (n > 0 && keys == NULL) return -2;
+    for (d = 0; d < ORACLE_BUCKETS; ++d) fill[d] = 0;
+    for (i = 0; i < n; ++i) {
+        const uint64_t key = width == 4 ? (uint64_t)((const uint32_t*)keys)[i] : ((const uint64_t*)keys)[i];
+        const unsigned b = (unsigned)((key >> shift) & 255u);
+        if (fill[b] < cap)
+            fill[b] += 1; /* lands in its estimated bucket */
+        else
+            over += 1;    /* the bucket is full: overflow */
+    }
+    *out = over;
+    return 0;
+}

@@ -3,7 +3,8 @@ oracle's pins catch every one of them.
 
 Each mutant is oracle.c with one textual edit (a dropped pass, a wrong prefix
 index, a wrong digit mask or shift, a payload dealt from the wrong slot, an
-unstable deal, a missing buffer swap).  It is compiled into a scratch library
+unstable deal, a missing buffer swap, an off-by-one bucket capacity in the
+estimated deal).  It is compiled into a scratch library
 and a battery of the pins from test_oracle_pins.py runs against it in a child
 process (so a mutant that writes out of bounds only kills the child).  The
 unmodified source must pass the same battery.
@@ -70,6 +71,18 @@ for dt, it, kt in ((np.float32, np.uint32, 0), (np.float64, np.uint64, 1)):
 a = g.integers(-4, 4, 500).astype(np.int32)
 k, v = orc.sort_format(3, 0x101, a, np.arange(500, dtype=np.uint32))
 assert v.tolist() == sorted(range(500), key=lambda i: (-a[i], i))
+for trial in range(8):
+    n = int(g.integers(0, 3000))
+    k = g.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
+    if trial % 2:
+        k &= np.uint32(0xFF3FFFFF)
+    cap = int(g.integers(0, 30))
+    cnt = np.bincount(((k >> np.uint32(16)) & np.uint32(255)).astype(np.int64), minlength=256)
+    assert orc.overflow_count(k, 16, cap) == int(np.maximum(cnt - cap, 0).sum())
+    k64 = k.astype(np.uint64) << np.uint64(32)
+    cnt = np.bincount(((k64 >> np.uint64(56)) & np.uint64(255)).astype(np.int64), minlength=256)
+    assert orc.overflow_count(k64, 56, cap) == int(np.maximum(cnt - cap, 0).sum())
+assert orc.overflow_count(np.full(100, 7, np.uint32), 0, 10) == 90
 print("PINS-PASS")
 """
 
@@ -93,6 +106,9 @@ MUTANTS = [
     ("static uint64_t fmt_encode(", "x = x ^ sign;", "x = x ^ (sign >> 1);"),
     ("static uint64_t fmt_decode(", "if (fmt & ORACLE_FMT_DESC) y = y ^ all;", ";"),
     ("static uint64_t fmt_decode(", "if (y & sign) y = y & ~sign;", "if (y & sign) y = y ^ all;"),
+    ("int oracle_overflow_count(", "if (fill[b] < cap)", "if (fill[b] <= cap)"),
+    ("int oracle_overflow_count(", "(unsigned)((key >> shift) & 255u)", "(unsigned)((key >> shift) & 127u)"),
+    ("int oracle_overflow_count(", "((const uint32_t*)keys)[i]", "((const uint32_t*)keys)[i] >> 1"),
 ]
 
 
