@@ -691,6 +691,10 @@ def main():
     ap.add_argument("--dists", default="", help="comma-separated subset of the workload's distributions")
     ap.add_argument("--requests", type=int, default=0, help="served workload: requests per pass")
     ap.add_argument("--serve-streams", type=int, default=4, help="served workload: server streams")
+    ap.add_argument("--schedule", default="plan", choices=["plan", "msd", "lsd", "dfr"],
+                    help="plain workloads: override the launch plan's schedule of the top digits "
+                         "(msd: diverting MSD; lsd: diverting LSD with one counting read; dfr: diverting "
+                         "LSD with the estimated first deal, Fast Radix)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.dists and "dists" in wl:
@@ -732,6 +736,11 @@ def main():
     vals = torch.empty_like(vals0) if kv else None
     sorter = dfr.Sorter(kt, n, dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    if args.schedule != "plan":
+        c = dfr.dfr_tune_class(n)
+        t = dfr.dfr_tune_get(kt, c)
+        t["schedule"] = {"msd": dfr.DFR_SCHED_MSD, "lsd": dfr.DFR_SCHED_LSD, "dfr": dfr.DFR_SCHED_DFR}[args.schedule]
+        dfr.check(dfr.dfr_tune_set(kt, c, t), "dfr_tune_set")
 
     def restore(d):
         work.copy_(pristine[d])
@@ -807,17 +816,27 @@ def main():
             prof[k] = (a + ms_k, b + n_k)
     dfr.dfr_profile_enable(False)
     rec = wbytes + vbytes
+    # The dominant deal kernel: the MSD levels' scatter, or the LSD passes
+    # when an LSD schedule dealt the top digits (read + write of every record
+    # dealt, per launch).
     scatter_keys = sum(sum(p["level_keys"]) for p in plan.values())
+    lsd_keys = sum(p["lsd_keys"] for p in plan.values())
     scatter_ms, scatter_launches = prof["scatter"]
-    scatter_bytes = 2 * rec * scatter_keys
-    achieved = scatter_bytes / (scatter_ms * 1e-3) / 1e9 if scatter_ms > 0 else 0.0
+    lsd_ms, lsd_launches = prof.get("lsd_pass", (0.0, 0))
+    if lsd_ms > scatter_ms:
+        dom_kernel, dom_ms, dom_launches, dom_keys = "k_lsd_pass", lsd_ms, lsd_launches, lsd_keys
+    else:
+        dom_kernel, dom_ms, dom_launches, dom_keys = "k_scatter", scatter_ms, scatter_launches, scatter_keys
+    dom_bytes = 2 * rec * dom_keys
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else 0.0
     traffic = None
-    if SCATTER_NCU_BYTES_PER_KEY is not None and not kv and SCATTER_SRC_SHA == kernel_source_sha():
+    if (SCATTER_NCU_BYTES_PER_KEY is not None and not kv and dom_kernel == "k_scatter"
+            and SCATTER_SRC_SHA == kernel_source_sha()):
         traffic = SCATTER_NCU_BYTES_PER_KEY * scatter_keys / max(1, scatter_launches)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "k_scatter",
+                "frac": achieved / peak, "traffic": traffic, "kernel": dom_kernel,
                 "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": scatter_bytes / max(1, scatter_launches)}
+                "algorithmic_bytes_per_launch": dom_bytes / max(1, dom_launches)}
     # Small arrays: the same sorts launched as one captured CUDA graph each
     # (dfr_graph_*), which replaces the call's kernel launches by one.
     graph_ms = {}
@@ -848,7 +867,11 @@ def main():
                        "cta_keys": p["cta_keys"], "wsort_keys": p["wsort_keys"], "tiny_keys": p["tiny_keys"],
                        "const_keys": p["const_keys"], "group_buckets": p["group_buckets"],
                        "cta_buckets": p["cta_buckets"], "wsort_buckets": p["wsort_buckets"],
+                       "schedule": ("msd", "lsd", "dfr")[p["schedule"]], "lsd_keys": p["lsd_keys"],
                        "kernel_ms": prof_by_dist[d]}
+        if p["est_capacity"]:
+            per_dist[d]["est_overflow"] = p["est_overflow"]
+            per_dist[d]["est_aborted"] = p["est_aborted"]
         if d in graph_ms:
             per_dist[d]["graph_ms"] = graph_ms[d]
             per_dist[d]["graph_gkeys_s"] = n / (graph_ms[d] * 1e-3) / 1e9
@@ -897,7 +920,8 @@ def main():
             "metric": "Gkeys/s", "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32" if not kv else "u64+u32", "data": "synthetic",
-            "config": dict(config_of(args.workload, wl), clocks="sampled every 200 ms over the warm-up and timed steps"),
+            "config": dict(config_of(args.workload, wl), schedule=args.schedule,
+                           clocks="sampled every 200 ms over the warm-up and timed steps"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "per_dist": per_dist, "kernels": kernel_share,
         }

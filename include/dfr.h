@@ -130,9 +130,19 @@ typedef struct {
     uint64_t model_bytes;                              /* minimal bytes of the executed plan */
     uint64_t wsort_buckets, wsort_keys;                /* diverted to the warp shared-memory sort */
     uint32_t device_error_site;                        /* first failed device check (0 = none; see dfr_api.cu) */
-    uint32_t reserved;
+    uint32_t schedule;                                 /* how the top digits were sorted: DFR_SCHED_MSD, _LSD or
+                                                          _DFR (an estimate that failed reports DFR_SCHED_MSD) */
     uint64_t group_buckets;                            /* diverted key-only buckets finished by one counting pass
                                                           plus in-group ranking */
+    uint64_t lsd_keys;                                 /* keys dealt by the LSD passes (both passes; includes the
+                                                          part of a failed estimated pass that ran) */
+    uint64_t est_overflow;                             /* keys the estimated deal sent to overflow regions */
+    uint32_t est_capacity;                             /* keys per estimated bucket (0 unless DFR_SCHED_DFR ran) */
+    uint32_t est_aborted;                              /* 1: an overflow region filled up and the MSD schedule
+                                                          sorted the array instead */
+    uint32_t root_read;                                /* 1: the root count read the keys (0 when the estimated
+                                                          deal counted them) */
+    uint32_t reserved2;
 } dfr_stats_t;
 
 /* dfr_get_stats -- wait for `stream` and copy the counters of the last call
@@ -337,8 +347,30 @@ typedef struct {
                                       ones to the CTA sort (128 .. 512) */
     uint32_t scatter_ctas_per_sm;  /* scatter grid: CTAs per SM, 0 = as many as fit */
     uint32_t ctasort_ctas_per_sm;  /* CTA-sort grid: CTAs per SM, 0 = as many as fit */
-    uint32_t reserved[3];          /* zero */
+    uint32_t schedule;             /* how a single array sorts its top two digits (DFR_SCHED_*); batches
+                                      always use DFR_SCHED_MSD */
+    uint32_t reserved[2];          /* zero */
 } dfr_tune_t;
+
+/*
+ * Schedules of the top digits (paper, Section "Diverting Fast Radix").
+ *   DFR_SCHED_MSD  every level counts its digit, then deals it (diverting MSD,
+ *                  the paper's Algorithm 2);
+ *   DFR_SCHED_LSD  one upfront read counts the top two digits; they are dealt
+ *                  least significant first, then the 16-bit prefix buckets are
+ *                  diverted or recursed on (diverting LSD, Algorithm 4);
+ *   DFR_SCHED_DFR  as DFR_SCHED_LSD, but the first deal uses estimated bucket
+ *                  sizes (N/256) with overflow regions instead of a counting
+ *                  read (Fast Radix, Algorithm 3); if an overflow region fills
+ *                  up, that deal is discarded and DFR_SCHED_MSD sorts the array.
+ * All three give the same result.  The LSD schedules apply to single arrays of
+ * at least 256 x the CTA-sort capacity keys (dfr_lsd_min_keys); smaller arrays
+ * and batches use DFR_SCHED_MSD whatever the plan says.
+ */
+#define DFR_SCHED_MSD 0
+#define DFR_SCHED_LSD 1
+#define DFR_SCHED_DFR 2
+uint64_t dfr_lsd_min_keys(int key_type);
 
 /* Size classes: 0 = mean array length below 2^12 keys, c = [2^(10+2c), 2^(12+2c)),
  * DFR_TUNE_CLASSES-1 = 2^28 keys and above. */
@@ -387,7 +419,7 @@ int dfr_set_debug(uint32_t spin_limit, int force_timeout);
  * device, returns per-kind totals and clears them.  Kinds are listed by
  * dfr_profile_kind_name(). */
 int dfr_profile_enable(int on);
-#define DFR_PROFILE_KINDS 11
+#define DFR_PROFILE_KINDS 13
 int dfr_profile_read(double* ms_total /*[DFR_PROFILE_KINDS]*/, uint64_t* launches /*[DFR_PROFILE_KINDS]*/);
 const char* dfr_profile_kind_name(int kind);
 

@@ -35,7 +35,7 @@ DFR_U32_KV = 3
 
 DFR_MAX_N = (1 << 30) - 1
 DFR_NOALLOC_MAX_N = 1 << 20
-DFR_PROFILE_KINDS = 11
+DFR_PROFILE_KINDS = 13
 DFR_STATS_MAX_LEVELS = 16
 DFR_SERVER_MAX_STREAMS = 64
 DFR_SERVER_MAX_INFLIGHT = 64
@@ -46,6 +46,9 @@ DFR_FMT_FLOAT = 2
 DFR_FMT_DESCENDING = 0x100
 DFR_TUNE_WARP_MIN = 128
 DFR_TUNE_WARP_MAX = 512
+DFR_SCHED_MSD = 0
+DFR_SCHED_LSD = 1
+DFR_SCHED_DFR = 2
 
 KEY_BYTES = {DFR_U32: 4, DFR_U64: 8, DFR_U64_KV: 8, DFR_U32_KV: 4}
 HAS_VALS = {DFR_U32: False, DFR_U64: False, DFR_U64_KV: True, DFR_U32_KV: True}
@@ -75,16 +78,17 @@ class dfr_stats_t(ctypes.Structure):
                 ("level_keys", _u64 * DFR_STATS_MAX_LEVELS), ("level_hist_keys", _u64 * DFR_STATS_MAX_LEVELS),
                 ("cta_buckets", _u64), ("cta_keys", _u64), ("tiny_buckets", _u64), ("tiny_keys", _u64),
                 ("const_buckets", _u64), ("const_keys", _u64), ("copy_keys", _u64), ("model_bytes", _u64),
-                ("wsort_buckets", _u64), ("wsort_keys", _u64), ("device_error_site", _u32), ("reserved", _u32),
-                ("group_buckets", _u64)]
+                ("wsort_buckets", _u64), ("wsort_keys", _u64), ("device_error_site", _u32), ("schedule", _u32),
+                ("group_buckets", _u64), ("lsd_keys", _u64), ("est_overflow", _u64), ("est_capacity", _u32),
+                ("est_aborted", _u32), ("root_read", _u32), ("reserved2", _u32)]
 
 
 class dfr_tune_t(ctypes.Structure):
     _fields_ = [("target_log2", _u32), ("max_bits", _u32), ("warp_max", _u32), ("scatter_ctas_per_sm", _u32),
-                ("ctasort_ctas_per_sm", _u32), ("reserved", _u32 * 3)]
+                ("ctasort_ctas_per_sm", _u32), ("schedule", _u32), ("reserved", _u32 * 2)]
 
 
-TUNE_FIELDS = ("target_log2", "max_bits", "warp_max", "scatter_ctas_per_sm", "ctasort_ctas_per_sm")
+TUNE_FIELDS = ("target_log2", "max_bits", "warp_max", "scatter_ctas_per_sm", "ctasort_ctas_per_sm", "schedule")
 
 _SIGNATURES = {
     "dfr_workspace_bytes": (ctypes.c_int, [ctypes.c_int, _u64, ctypes.POINTER(_sz)]),
@@ -112,6 +116,7 @@ _SIGNATURES = {
     "dfr_graph_launch": (ctypes.c_int, [_vp, _vp]),
     "dfr_graph_destroy": (ctypes.c_int, [_vp]),
     "dfr_tune_class": (ctypes.c_int, [_u64]),
+    "dfr_lsd_min_keys": (_u64, [ctypes.c_int]),
     "dfr_tune_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(dfr_tune_t)]),
     "dfr_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(dfr_tune_t)]),
     "dfr_tune_reset": (ctypes.c_int, []),
@@ -354,13 +359,19 @@ def dfr_tune_get(key_type: int, size_class: int) -> dict:
 
 
 def dfr_tune_set(key_type: int, size_class: int, tune: dict) -> int:
-    """Override one entry of the launch-plan table (fields as dfr_tune_get)."""
-    t = dfr_tune_t(*(int(tune[f]) for f in TUNE_FIELDS))
+    """Override one entry of the launch-plan table (fields as dfr_tune_get;
+    a missing "schedule" means DFR_SCHED_MSD)."""
+    t = dfr_tune_t(*(int(tune.get(f, 0) if f == "schedule" else tune[f]) for f in TUNE_FIELDS))
     return load().dfr_tune_set(int(key_type), int(size_class), ctypes.byref(t))
 
 
 def dfr_tune_reset() -> int:
     return load().dfr_tune_reset()
+
+
+def dfr_lsd_min_keys(key_type: int) -> int:
+    """Smallest single array the LSD schedules (DFR_SCHED_LSD / _DFR) apply to."""
+    return int(load().dfr_lsd_min_keys(int(key_type)))
 
 
 def dfr_set_debug(spin_limit: int = 0, force_timeout: bool = False) -> int:

@@ -53,7 +53,8 @@ bool tune_valid(const dfr_tune_t& t) {
   if (t.max_bits < 4 || t.max_bits > (uint32_t)RB) return false;
   if (t.warp_max < DFR_TUNE_WARP_MIN || t.warp_max > DFR_TUNE_WARP_MAX) return false;
   if (t.scatter_ctas_per_sm > 4 || t.ctasort_ctas_per_sm > 4) return false;
-  return t.reserved[0] == 0 && t.reserved[1] == 0 && t.reserved[2] == 0;
+  if (t.schedule > DFR_SCHED_DFR) return false;
+  return t.reserved[0] == 0 && t.reserved[1] == 0;
 }
 
 }  // namespace
@@ -162,6 +163,16 @@ using namespace dfr;
 
 extern "C" {
 
+uint64_t dfr_lsd_min_keys(int key_type) {
+  switch (key_type) {
+    case DFR_U32: return lsd_min_n<uint32_t, NoVal>();
+    case DFR_U32_KV: return lsd_min_n<uint32_t, uint32_t>();
+    case DFR_U64: return lsd_min_n<uint64_t, NoVal>();
+    case DFR_U64_KV: return lsd_min_n<uint64_t, uint32_t>();
+    default: return 0;
+  }
+}
+
 int dfr_workspace_bytes(int key_type, uint64_t n, size_t* bytes) {
   if (!bytes || n > DFR_MAX_N) return DFR_ERR_INVALID_ARG;
   return ws_typed(key_type, n, 1u, bytes);
@@ -231,15 +242,25 @@ int dfr_get_stats(const void* ws, dfr_stream_t stream, dfr_stats_t* out) {
   // a read and a write of every record sorted by a diversion sort; a read and
   // a write of every constant record that has to move back from the buffer.
   // Re-reads by per-level counts are not charged (they could be fused).
+  // The LSD passes charge a read and a write of every record they deal; when
+  // the estimated deal counted the keys the root count read nothing.
   const uint64_t rec = (uint64_t)h.key_bytes + h.val_bytes;
-  uint64_t b = h.n_total * h.key_bytes;
+  uint64_t b = h.root_skipped ? 0 : h.n_total * h.key_bytes;
+  b += 2 * rec * h.lsd_keys;
   for (int L = 0; L < MAXLV; ++L) b += 2 * rec * h.lv[L].keys;
   b += 2 * rec * (h.cta_keys + h.wsort_keys + h.tiny_keys + h.copy_keys);
   out->model_bytes = b;
   out->wsort_buckets = h.wsort_buckets;
-  // 1 scatter staging, 2 scatter write, 3 CTA-sort staging, 4 warp-sort staging, 5 look-back timeout
+  // 1 scatter staging, 2 scatter write, 3 CTA-sort staging, 4 warp-sort staging, 5 look-back timeout,
+  // 6 LSD-pass staging, 7 LSD-pass write, 8 a segment histogram that does not add up
   out->device_error_site = h.err_site;
   out->group_buckets = h.group_buckets;
+  out->schedule = h.sched;
+  out->lsd_keys = h.lsd_keys;
+  out->est_overflow = h.est_overflow;
+  out->est_capacity = h.est_cap;
+  out->est_aborted = h.est_abort;
+  out->root_read = h.n_total ? (h.root_skipped ? 0u : 1u) : 0u;
   out->wsort_keys = h.wsort_keys;
   return DFR_OK;
 }
@@ -397,7 +418,8 @@ int dfr_profile_read(double* ms_total, uint64_t* launches) {
 const char* dfr_profile_kind_name(int kind) {
   static const char* names[DFR_PROFILE_KINDS] = {"init",     "root_count", "root_classify", "level_count",
                                                   "scatter",  "classify",   "ctasort",       "copy",
-                                                  "h2d",      "warpsort",     "keyfmt"};
+                                                  "h2d",      "warpsort",     "keyfmt",        "lsd_pass",
+                                                  "lsd_plan"};
   return (kind >= 0 && kind < DFR_PROFILE_KINDS) ? names[kind] : "unknown";
 }
 

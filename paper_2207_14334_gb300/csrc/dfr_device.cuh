@@ -62,10 +62,12 @@ constexpr uint32_t T_WARP = 32;  // tiny-bucket threshold (warp sort)
 enum : uint32_t { DERR_TIMEOUT = 1u, DERR_BOUNDS = 2u, DERR_CAPACITY = 4u };
 enum : uint32_t {
   ERR_SITE_SCATTER_STAGE = 1u, ERR_SITE_SCATTER_WRITE, ERR_SITE_CTASORT_STAGE, ERR_SITE_WARPSORT_STAGE,
-  ERR_SITE_LOOKBACK
+  ERR_SITE_LOOKBACK, ERR_SITE_LSD_STAGE, ERR_SITE_LSD_WRITE, ERR_SITE_CLASSIFY
 };
 constexpr uint32_t NO_OWNER = 0xffffffffu;  // tile-owner entry of a tile that must be skipped
-enum : uint32_t { SEG_NEEDS_HIST = 1u, SEG_NEEDS_ANDOR = 2u };
+// SEG_PREDEALT: a level-0 segment made by the LSD top phase, whose keys are
+// already dealt on its window (k_classify only classifies its buckets).
+enum : uint32_t { SEG_NEEDS_HIST = 1u, SEG_NEEDS_ANDOR = 2u, SEG_PREDEALT = 4u };
 enum : uint32_t { ITEM_PARITY = 1u, ITEM_COPY = 2u };
 
 struct NoVal {};
@@ -142,6 +144,13 @@ struct Ctl {
   unsigned long long tiny_buckets, tiny_keys;
   unsigned long long const_buckets, const_keys;
   unsigned long long copy_keys;
+  // LSD top phase (single-array calls whose plan asks for it)
+  uint32_t sched;         // schedule that sorted the top digits: 0 MSD, 1 LSD, 2 LSD with estimated deal
+  uint32_t est_abort;     // the estimated deal gave up (an overflow region filled up)
+  uint32_t root_skipped;  // the root count did not read the keys (the estimated deal counted them)
+  uint32_t est_cap;       // estimated bucket size of the estimated deal
+  unsigned long long lsd_keys;      // keys dealt by the LSD passes (both passes)
+  unsigned long long est_overflow;  // keys the estimated deal sent to an overflow region
   LevelCtl lv[MAXLV + 1];
 };
 
@@ -150,6 +159,29 @@ struct RootAcc {
   K nand;  // OR of ~key  (AND = ~nand; zero-initialised)
   K orv;   // OR of key
   uint32_t hist[M];  // histogram of the top byte
+};
+
+// State of the LSD top phase of one single-array call (Section "Diverting
+// Fast Radix", Algorithms 3-4): the two top digits D0 = bits [W-8, W) and
+// D1 = bits [W-16, W-8) are dealt least significant first -- D1 into the
+// buffer, then D0 back into the array -- after which the buckets of the
+// 16-bit prefix are diverted or recursed on by the MSD levels.  Zeroed by
+// k_init.
+struct LsdCtl {
+  uint32_t on;        // 1: the LSD phase sorts the top digits (else the MSD schedule runs alone)
+  uint32_t abort;     // mode 2: an overflow region filled up; the estimated deal is discarded
+  uint32_t claim[2];  // tile claims of the two passes
+  uint32_t tiles_b;   // tiles of the second pass
+  uint32_t pad[3];
+  unsigned long long orv, nand;  // mode 2: OR / NOT-AND of the keys, gathered by the estimated deal
+  unsigned long long overflow;   // mode 2: keys sent to an overflow region
+  uint32_t cur1[M];   // key-only first pass: keys of each D1 digit placed so far (fill cursors)
+  uint32_t h0[M];     // D0 histogram (mode 2: counted by the estimated deal)
+  uint32_t h1[M];     // mode 1: D1 histogram, counted by the root count
+  uint32_t base0[M];  // exclusive scan of h0
+  uint32_t base1[M];  // mode 1: exclusive scan of h1
+  uint32_t pstart[2 * M + 1];         // first second-pass tile of each piece (and the total)
+  uint32_t poff[2 * M], plen[2 * M];  // piece 2d: D1 bucket d in buf; 2d+1: its overflow region
 };
 
 // Device view of the workspace; passed by value to every kernel.
@@ -175,6 +207,16 @@ struct Ctx {
   uint32_t target;    // buckets of about this many keys per radix window
   uint32_t max_bits;  // radix bits per level (<= RB)
   uint32_t warp_max;  // runs of at most this many keys go to the warp sort (<= its capacity)
+  // LSD top phase of a single-array call (lsd_mode 0 = MSD schedule only)
+  uint32_t lsd_mode;      // 0 off, 1 LSD with counted digits, 2 LSD with the estimated first deal
+  uint32_t est_cap;       // mode 2: keys per estimated bucket (multiple of 16, M * est_cap <= n)
+  uint32_t est_ocap;      // mode 2: overflow slots per bucket (multiple of 16)
+  uint32_t lsd_tiles_a;   // tiles of the first pass (the array in TILE-key tiles)
+  uint32_t lsd_tiles_b_cap;  // look-back words (per digit) reserved for the second pass
+  LsdCtl* lsd;
+  uint32_t* lsd_st[2];    // look-back words of the two passes ([tiles][M]; pass 0 only for key-value)
+  void* pool_k;           // mode 2: overflow regions, M x est_ocap keys
+  uint32_t* pool_v;       //          and payloads
 };
 
 // ------------------------------------------------------------------ helpers
@@ -496,10 +538,12 @@ __device__ __forceinline__ uint32_t window_bits(const Ctx& c, uint32_t len, uint
 
 // ------------------------------------------------------------------ kernels
 
-// Zero the control block and the per-array root accumulators; for a plain
-// call also store the single array descriptor.
+// Zero the control block and the per-array root accumulators (and, when
+// `z16` > 0, the LSD top phase's control block and look-back words: z16
+// 16-byte words from `z`); for a plain call also store the single array
+// descriptor.
 template <class K>
-__global__ void k_init(Ctx c, ArrDesc a0, int write_a0, uint32_t root_words) {
+__global__ void k_init(Ctx c, ArrDesc a0, int write_a0, uint32_t root_words, uint4* z, uint32_t z16) {
   const uint32_t ctl_words = sizeof(Ctl) / 4;
   uint32_t* cw = reinterpret_cast<uint32_t*>(c.ctl);
   uint32_t* rw = reinterpret_cast<uint32_t*>(c.root);
@@ -510,6 +554,8 @@ __global__ void k_init(Ctx c, ArrDesc a0, int write_a0, uint32_t root_words) {
     else
       rw[i - ctl_words] = 0u;
   }
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < z16; i += gridDim.x * blockDim.x)
+    z[i] = make_uint4(0u, 0u, 0u, 0u);
   if (write_a0 && blockIdx.x == 0 && threadIdx.x == 0) c.arrs[0] = a0;
 }
 
@@ -519,9 +565,10 @@ __global__ void k_init(Ctx c, ArrDesc a0, int write_a0, uint32_t root_words) {
 // that hit one counter are serialised by the hardware, which measured faster
 // than aggregating them in software on every input, skewed or sorted ones
 // included), and OR / NOT-AND of the keys into orv / nandv.
-template <class K>
+template <class K, bool TWO = false>
 __device__ __forceinline__ void warp_count_range(const K* src, uint32_t lo, uint32_t hi, uint32_t shift,
-                                                 bool do_hist, uint32_t* wh, K& orv, K& nandv) {
+                                                 bool do_hist, uint32_t* wh, K& orv, K& nandv,
+                                                 uint32_t* wh2 = nullptr, uint32_t shift2 = 0) {
   constexpr uint32_t VK = 16 / sizeof(K);
   constexpr int BATCH = 8;
   const uint32_t lane = lane_id();
@@ -535,6 +582,9 @@ __device__ __forceinline__ void warp_count_range(const K* src, uint32_t lo, uint
       nandv |= ~k;
     }
     if (do_hist && valid) atomicAdd(&wh[digit_of(k, shift)], 1u);
+    if constexpr (TWO) {
+      if (valid) atomicAdd(&wh2[digit_of(k, shift2)], 1u);
+    }
   };
   {
     const bool valid = lane < head;
@@ -597,23 +647,37 @@ __device__ __forceinline__ void atomic_or_key(K* p, K v) {
 // and the histogram of its top byte (the initial counting pass, Alg. 1).
 // Every warp claims whole tiles on its own and keeps private counters and
 // OR/NOT-AND registers, flushed only when its next tile belongs to another
-// array -- no block-wide barrier.
-template <class K, int NT, int TILE>
-__global__ void __launch_bounds__(NT) k_root_count(Ctx c, uint32_t root_tiles) {
+// array -- no block-wide barrier.  With TWO (the LSD schedule of a
+// single-array call) the same read also counts the second byte into h2: all
+// the digit histograms the LSD passes need come from one upfront read (Alg. 4).
+// When the estimated deal already counted the keys (LSD mode 2), it does
+// nothing.
+template <class K, int NT, int TILE, bool TWO>
+__global__ void __launch_bounds__(NT) k_root_count(Ctx c, uint32_t root_tiles, uint32_t* h2) {
   constexpr int NW = NT / 32;
   constexpr uint32_t TOP = 8 * sizeof(K) - RB;
   __shared__ uint32_t s_h[NW * M];
+  __shared__ uint32_t s_h2[TWO ? NW * M : 1];
+  if (c.lsd_mode == 2u && ld_relaxed(&c.lsd->on) != 0u) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.ctl->root_skipped = 1u;
+    return;
+  }
   RootAcc<K>* root = reinterpret_cast<RootAcc<K>*>(c.root);
   const uint32_t lane = lane_id();
   uint32_t* wh = s_h + (threadIdx.x >> 5) * M;
+  uint32_t* wh2 = s_h2 + (TWO ? (threadIdx.x >> 5) * M : 0u);
 #pragma unroll
-  for (int i = 0; i < M / 32; ++i) wh[i * 32 + lane] = 0u;
+  for (int i = 0; i < M / 32; ++i) {
+    wh[i * 32 + lane] = 0u;
+    if constexpr (TWO) wh2[i * 32 + lane] = 0u;
+  }
   __syncwarp();
   uint32_t cur = 0xffffffffu;
   K orv = 0, nandv = 0;
   auto flush = [&]() {
     if (cur == 0xffffffffu) return;
     warp_flush_hist(wh, root[cur].hist);
+    if constexpr (TWO) warp_flush_hist(wh2, h2);
     const K o = warp_or(orv), na = warp_or(nandv);
     if (lane == 0) {
       atomic_or_key(&root[cur].orv, o);
@@ -643,7 +707,7 @@ __global__ void __launch_bounds__(NT) k_root_count(Ctx c, uint32_t root_tiles) {
     const uint32_t j = t - ad.root_tile_start;
     const uint32_t b = j * (uint32_t)TILE;
     const uint32_t e = min(ad.n, b + (uint32_t)TILE);
-    warp_count_range<K>(reinterpret_cast<const K*>(ad.keys), b, e, TOP, true, wh, orv, nandv);
+    warp_count_range<K, TWO>(reinterpret_cast<const K*>(ad.keys), b, e, TOP, true, wh, orv, nandv, wh2, TOP - RB);
   }
   flush();
 }
@@ -718,6 +782,7 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
     const ArrDesc ad = c.arrs[a];
     const uint32_t n = ad.n;
     if (n <= 1) continue;
+    if (c.lsd_mode != 0u && a == 0u && c.lsd->on != 0u) continue;  // the LSD top phase sorts it
     const K orv = root[a].orv;
     const K andv = ~root[a].nand;
     if (orv == andv) {
@@ -885,15 +950,15 @@ __device__ __forceinline__ bool seg_is_dealt(const Seg& seg) {
 // counts of the earlier tiles of the segment back to the first inclusive
 // prefix, then publishes this tile's inclusive prefix.  Every wait is bounded
 // by c.spin_limit; a wait that runs out records DERR_TIMEOUT and sets *fail.
-__device__ __forceinline__ uint32_t look_back(const Ctx& c, uint32_t t, uint32_t tile_start, uint32_t d,
-                                              uint32_t tcount, uint32_t* fail) {
-  uint32_t* st = c.status + (size_t)t * M;
+__device__ __forceinline__ uint32_t look_back(const Ctx& c, uint32_t* status, uint32_t t, uint32_t tile_start,
+                                              uint32_t d, uint32_t tcount, uint32_t* fail) {
+  uint32_t* st = status + (size_t)t * M;
   uint32_t excl = 0;
   if (t > tile_start) {
     bool ok = true;
     uint32_t tp = t - 1;
     for (;;) {
-      const uint32_t* p = c.force_timeout ? &c.ctl->never : c.status + (size_t)tp * M + d;
+      const uint32_t* p = c.force_timeout ? &c.ctl->never : status + (size_t)tp * M + d;
       uint32_t x = ld_relaxed(p);
       uint32_t spins = 0;
       while ((x >> 30) == 0u) {
@@ -1063,7 +1128,7 @@ __global__ void __launch_bounds__(NT, (std::is_same<V, NoVal>::value ? 3 : 2)) k
       // each bucket with one atomic on the bucket's fill cursor.
       uint32_t excl;
       if constexpr (KV)
-        excl = look_back(c, t, seg.tile_start, threadIdx.x, tcount, &s_fail);
+        excl = look_back(c, c.status, t, seg.tile_start, threadIdx.x, tcount, &s_fail);
       else
         excl = tcount ? atomicAdd(&cur[(size_t)s * M + threadIdx.x], tcount) : 0u;
       s_tstart[threadIdx.x] = tstart;
@@ -1224,127 +1289,134 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
       }
     } else {
       const uint32_t cnt = hist[(size_t)s * M + d];
-      const uint32_t excl = scan256(cnt, s_scan, nullptr);
-      if (threadIdx.x == 0) atomicAdd(&ctl->lv[L].keys, (unsigned long long)seg.len);
-      const uint32_t off = seg.off + excl;
-      const uint32_t pout = seg.parity ^ 1u;
-      // Large buckets go to the next level (or, when every bit is consumed,
-      // they are constant and only move back if they sit in the buffer).
-      if (cnt > (uint32_t)TCTA) {
-        if (seg.shift == 0u) {
-          atomicAdd(&s_stat[0], 1ull);
-          atomicAdd(&s_stat[1], (unsigned long long)cnt);
-          if (pout) {
-            atomicAdd(&s_stat[2], (unsigned long long)cnt);
-            // the bucket's keys are the segment prefix with this digit
-            const K val = (K)(((K)seg.orv & ~(((K)(M - 1)) << seg.shift)) | ((K)d << seg.shift));
-            add_copy(off, cnt, seg.arr, (unsigned long long)val);
-          }
-        } else {
-          // the bucket's varying bits all lie below the parent's window
-          const uint32_t b = window_bits(c, cnt, seg.shift, L + 1);
-          const uint32_t shift = seg.shift > b ? seg.shift - b : 0u;
-          add_big(off, cnt, seg.arr, shift, seg.shift - shift, pout, SEG_NEEDS_HIST | SEG_NEEDS_ANDOR, 0ull, 0ull);
-        }
-      }
-      // Small buckets are diverted in bulk: consecutive ones (in digit order,
-      // hence adjacent in memory and ordered) are joined into runs of at
-      // most TCTA keys and each run is sorted as one item -- sorting the run
-      // sorts every bucket in it, and equal keys never span two buckets.
-      s_bcnt[d] = cnt > (uint32_t)TCTA ? 0xffffffffu : cnt;
-      s_boff[d] = off;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        uint32_t nr = 0, roff = 0, rlen = 0;
-        for (uint32_t x = 0; x < (uint32_t)M; ++x) {
-          const uint32_t cx = s_bcnt[x];
-          if (cx == 0u) continue;
-          if (cx == 0xffffffffu || rlen + cx > (uint32_t)TCTA) {
-            if (rlen) {
-              s_run_off[nr] = roff;
-              s_run_len[nr] = rlen;
-              ++nr;
+      uint32_t tot = 0;
+      const uint32_t excl = scan256(cnt, s_scan, &tot);
+      // A histogram that does not add up to the segment (only after a failed
+      // device check upstream) must not become buckets: skip the segment.
+      if (tot != seg.len) {
+        if (threadIdx.x == 0) record_error(ctl, DERR_BOUNDS, ERR_SITE_CLASSIFY);
+      } else {
+        if (threadIdx.x == 0 && !(seg.flags & SEG_PREDEALT)) atomicAdd(&ctl->lv[L].keys, (unsigned long long)seg.len);
+        const uint32_t off = seg.off + excl;
+        const uint32_t pout = seg.parity ^ 1u;
+        // Large buckets go to the next level (or, when every bit is consumed,
+        // they are constant and only move back if they sit in the buffer).
+        if (cnt > (uint32_t)TCTA) {
+          if (seg.shift == 0u) {
+            atomicAdd(&s_stat[0], 1ull);
+            atomicAdd(&s_stat[1], (unsigned long long)cnt);
+            if (pout) {
+              atomicAdd(&s_stat[2], (unsigned long long)cnt);
+              // the bucket's keys are the segment prefix with this digit
+              const K val = (K)(((K)seg.orv & ~(((K)(M - 1)) << seg.shift)) | ((K)d << seg.shift));
+              add_copy(off, cnt, seg.arr, (unsigned long long)val);
             }
-            rlen = 0;
-            if (cx == 0xffffffffu) continue;
+          } else {
+            // the bucket's varying bits all lie below the parent's window
+            const uint32_t b = window_bits(c, cnt, seg.shift, L + 1);
+            const uint32_t shift = seg.shift > b ? seg.shift - b : 0u;
+            add_big(off, cnt, seg.arr, shift, seg.shift - shift, pout, SEG_NEEDS_HIST | SEG_NEEDS_ANDOR, 0ull, 0ull);
           }
-          if (rlen == 0) roff = s_boff[x];
-          rlen += cx;
         }
-        if (rlen) {
-          s_run_off[nr] = roff;
-          s_run_len[nr] = rlen;
-          ++nr;
-        }
-        s_nrun = nr;
-        s_qn[0] = 0;
-        s_qn[1] = 0;
-      }
-      __syncthreads();
-      const uint32_t nr = s_nrun;
-      // run classes: single key, tiny (warp sort here), warp-sort queue, CTA queue
-      uint32_t rcls = 0, rloc = 0, rlen = 0, roff = 0;
-      bool rcopy = false;
-      if (threadIdx.x < nr) {
-        roff = s_run_off[threadIdx.x];
-        rlen = s_run_len[threadIdx.x];
-        if (seg.shift == 0u) {
-          // The window reached bit 0: every bucket of the run holds one
-          // repeated key (§MSD).  The run is final where it lies, or only
-          // moves back from the buffer: the tiny pass copies up to a warp of
-          // keys, a CTA-queue copy item the rest.
-          atomicAdd(&s_stat[0], 1ull);
-          atomicAdd(&s_stat[1], (unsigned long long)rlen);
-          if (pout) {
-            atomicAdd(&s_stat[2], (unsigned long long)rlen);
-            if (rlen <= T_WARP) {
-              rcls = 1;
-            } else {
-              rcls = 4;
-              rcopy = true;
-              rloc = atomicAdd(&s_qn[1], 1u);
+        // Small buckets are diverted in bulk: consecutive ones (in digit order,
+        // hence adjacent in memory and ordered) are joined into runs of at
+        // most TCTA keys and each run is sorted as one item -- sorting the run
+        // sorts every bucket in it, and equal keys never span two buckets.
+        s_bcnt[d] = cnt > (uint32_t)TCTA ? 0xffffffffu : cnt;
+        s_boff[d] = off;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          uint32_t nr = 0, roff = 0, rlen = 0;
+          for (uint32_t x = 0; x < (uint32_t)M; ++x) {
+            const uint32_t cx = s_bcnt[x];
+            if (cx == 0u) continue;
+            if (cx == 0xffffffffu || rlen + cx > (uint32_t)TCTA) {
+              if (rlen) {
+                s_run_off[nr] = roff;
+                s_run_len[nr] = rlen;
+                ++nr;
+              }
+              rlen = 0;
+              if (cx == 0xffffffffu) continue;
             }
+            if (rlen == 0) roff = s_boff[x];
+            rlen += cx;
           }
-        } else if (rlen == 1u) {
-          atomicAdd(&s_stat[0], 1ull);
-          atomicAdd(&s_stat[1], 1ull);
-          if (pout) {
-            atomicAdd(&s_stat[2], 1ull);
-            rcls = 1;  // a single key in the buffer: copied by the tiny pass
+          if (rlen) {
+            s_run_off[nr] = roff;
+            s_run_len[nr] = rlen;
+            ++nr;
           }
-        } else if (rlen <= T_WARP) {
-          rcls = 2;
-          atomicAdd(&s_stat[3], 1ull);
-          atomicAdd(&s_stat[4], (unsigned long long)rlen);
-        } else if (rlen <= c.warp_max) {
-          rcls = 3;
-          rloc = atomicAdd(&s_qn[0], 1u);
-          atomicAdd(&s_stat[8], 1ull);
-          atomicAdd(&s_stat[7], (unsigned long long)rlen);
-        } else {
-          rcls = 4;
-          rloc = atomicAdd(&s_qn[1], 1u);
-          atomicAdd(&s_stat[5], 1ull);
-          atomicAdd(&s_stat[6], (unsigned long long)rlen);
+          s_nrun = nr;
+          s_qn[0] = 0;
+          s_qn[1] = 0;
         }
-        if (rcls == 1 || rcls == 2) {
-          const uint32_t i = atomicAdd(&s_tiny_n, 1u);
-          s_tiny_off[i] = roff;
-          s_tiny_len[i] = rlen | (rcls == 1 ? 0x80000000u : 0u);
+        __syncthreads();
+        const uint32_t nr = s_nrun;
+        // run classes: single key, tiny (warp sort here), warp-sort queue, CTA queue
+        uint32_t rcls = 0, rloc = 0, rlen = 0, roff = 0;
+        bool rcopy = false;
+        if (threadIdx.x < nr) {
+          roff = s_run_off[threadIdx.x];
+          rlen = s_run_len[threadIdx.x];
+          if (seg.shift == 0u) {
+            // The window reached bit 0: every bucket of the run holds one
+            // repeated key (§MSD).  The run is final where it lies, or only
+            // moves back from the buffer: the tiny pass copies up to a warp of
+            // keys, a CTA-queue copy item the rest.
+            atomicAdd(&s_stat[0], 1ull);
+            atomicAdd(&s_stat[1], (unsigned long long)rlen);
+            if (pout) {
+              atomicAdd(&s_stat[2], (unsigned long long)rlen);
+              if (rlen <= T_WARP) {
+                rcls = 1;
+              } else {
+                rcls = 4;
+                rcopy = true;
+                rloc = atomicAdd(&s_qn[1], 1u);
+              }
+            }
+          } else if (rlen == 1u) {
+            atomicAdd(&s_stat[0], 1ull);
+            atomicAdd(&s_stat[1], 1ull);
+            if (pout) {
+              atomicAdd(&s_stat[2], 1ull);
+              rcls = 1;  // a single key in the buffer: copied by the tiny pass
+            }
+          } else if (rlen <= T_WARP) {
+            rcls = 2;
+            atomicAdd(&s_stat[3], 1ull);
+            atomicAdd(&s_stat[4], (unsigned long long)rlen);
+          } else if (rlen <= c.warp_max) {
+            rcls = 3;
+            rloc = atomicAdd(&s_qn[0], 1u);
+            atomicAdd(&s_stat[8], 1ull);
+            atomicAdd(&s_stat[7], (unsigned long long)rlen);
+          } else {
+            rcls = 4;
+            rloc = atomicAdd(&s_qn[1], 1u);
+            atomicAdd(&s_stat[5], 1ull);
+            atomicAdd(&s_stat[6], (unsigned long long)rlen);
+          }
+          if (rcls == 1 || rcls == 2) {
+            const uint32_t i = atomicAdd(&s_tiny_n, 1u);
+            s_tiny_off[i] = roff;
+            s_tiny_len[i] = rlen | (rcls == 1 ? 0x80000000u : 0u);
+          }
         }
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        s_qbase[0] = s_qn[0] ? atomicAdd(&ctl->wq_count, s_qn[0]) : 0u;
-        s_qbase[1] = s_qn[1] ? atomicAdd(&ctl->cta_count, s_qn[1]) : 0u;
-      }
-      __syncthreads();
-      if (rcls >= 3) {
-        const uint32_t q = s_qbase[rcls - 3] + rloc;
-        if (q < (rcls == 3 ? c.wqcap : c.ctacap))
-          (rcls == 3 ? c.w_q : c.cta_q)[q] = Item{roff, rlen, seg.arr, pout | (rcopy ? ITEM_COPY : 0u)};
-        else
-          atomicOr(&ctl->err, DERR_CAPACITY);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          s_qbase[0] = s_qn[0] ? atomicAdd(&ctl->wq_count, s_qn[0]) : 0u;
+          s_qbase[1] = s_qn[1] ? atomicAdd(&ctl->cta_count, s_qn[1]) : 0u;
+        }
+        __syncthreads();
+        if (rcls >= 3) {
+          const uint32_t q = s_qbase[rcls - 3] + rloc;
+          if (q < (rcls == 3 ? c.wqcap : c.ctacap))
+            (rcls == 3 ? c.w_q : c.cta_q)[q] = Item{roff, rlen, seg.arr, pout | (rcopy ? ITEM_COPY : 0u)};
+          else
+            atomicOr(&ctl->err, DERR_CAPACITY);
+        }
       }
     }
     __syncthreads();

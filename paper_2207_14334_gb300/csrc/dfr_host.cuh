@@ -6,12 +6,14 @@
 #pragma once
 
 #include <algorithm>
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <vector>
 
 #include "dfr.h"
 #include "dfr_device.cuh"
+#include "dfr_lsd.cuh"
 
 namespace dfr {
 
@@ -36,7 +38,7 @@ int rt_sms();
 dfr_tune_t rt_tune(int key_type, uint64_t mean_keys);
 
 enum ProfKind { PK_INIT = 0, PK_ROOT_COUNT, PK_ROOT_CLASSIFY, PK_LEVEL_COUNT, PK_SCATTER, PK_CLASSIFY, PK_CTASORT,
-                PK_COPY, PK_H2D, PK_WARPSORT, PK_KEYFMT };
+                PK_COPY, PK_H2D, PK_WARPSORT, PK_KEYFMT, PK_LSD_PASS, PK_LSD_PLAN };
 
 inline bool fmt_valid(int fmt) {
   return (fmt & ~(0xFF | DFR_FMT_DESCENDING)) == 0 && (fmt & 0xFF) <= DFR_FMT_FLOAT;
@@ -69,9 +71,22 @@ struct Cfg<uint64_t, uint32_t> {
 struct Layout {
   size_t ctl, arrs, root, segs0, segs1, hist0, hist1, cur0, cur1, owner, status, ctaq, wq, copyq, copyowner, total;
   uint32_t segcap, tilecap, ctacap, wqcap, copycap, copytilecap;
+  // LSD top phase (single arrays of at least lsd_min_n keys)
+  bool has_lsd;
+  size_t lsd, lsd_st0, lsd_st1, pool_k, pool_v;
+  uint32_t lsd_zero16;  // 16-byte words zeroed by k_init from `lsd` (control block + look-back words)
+  uint32_t lsd_tiles_a, lsd_tiles_b_cap, est_cap, est_ocap;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Smallest single array the LSD top phase takes: below M x T_CTA keys one
+// digit already brings buckets under the CTA-sort capacity (d = 1), where the
+// LSD and MSD schedules coincide.
+template <class K, class V>
+constexpr uint64_t lsd_min_n() {
+  return (uint64_t)M * Cfg<K, V>::CNT * Cfg<K, V>::CKPT;
+}
 
 template <class K, class V>
 Layout make_layout(uint64_t ntot, uint32_t narr) {
@@ -121,6 +136,28 @@ Layout make_layout(uint64_t ntot, uint32_t narr) {
   o = align256(o + (size_t)l.copycap * sizeof(CopyItem));
   l.copyowner = o;
   o = align256(o + (size_t)l.copytilecap * 4);
+  l.has_lsd = narr == 1u && ntot >= lsd_min_n<K, V>();
+  if (l.has_lsd) {
+    l.lsd_tiles_a = (uint32_t)((ntot + TILE - 1) / TILE);
+    // second-pass tiles: every one of the 2M pieces adds at most two partial tiles
+    l.lsd_tiles_b_cap = (uint32_t)(ntot / TILE) + 4u * M + 1u;
+    l.est_cap = (uint32_t)(ntot / M) & ~15u;
+    // overflow slots per bucket: 8 standard deviations of a uniform bucket's
+    // count (binomial, about sqrt(N/M)) plus a margin, at least N/(32 M)
+    const uint64_t sd8 = 8ull * (uint64_t)std::ceil(std::sqrt((double)ntot / M)) + 64ull;
+    l.est_ocap = (uint32_t)((std::max<uint64_t>(ntot / (32ull * M), sd8) + 15ull) & ~15ull);
+    l.lsd = o;
+    o = align256(o + sizeof(LsdCtl));
+    l.lsd_st0 = o;
+    o = align256(o + (KV ? (size_t)l.lsd_tiles_a * M * 4 : 0));
+    l.lsd_st1 = o;
+    o = align256(o + (size_t)l.lsd_tiles_b_cap * M * 4);
+    l.lsd_zero16 = (uint32_t)((o - l.lsd) / 16);
+    l.pool_k = o;
+    o = align256(o + (size_t)M * l.est_ocap * sizeof(K));
+    l.pool_v = o;
+    o = align256(o + (KV ? (size_t)M * l.est_ocap * 4 : 0));
+  }
   l.total = o;
   return l;
 }
@@ -150,6 +187,17 @@ inline Ctx make_ctx(void* ws, const Layout& l, uint32_t narr) {
   c.wqcap = l.wqcap;
   c.copycap = l.copycap;
   c.copytilecap = l.copytilecap;
+  if (l.has_lsd) {
+    c.lsd = reinterpret_cast<LsdCtl*>(b + l.lsd);
+    c.lsd_st[0] = reinterpret_cast<uint32_t*>(b + l.lsd_st0);
+    c.lsd_st[1] = reinterpret_cast<uint32_t*>(b + l.lsd_st1);
+    c.pool_k = b + l.pool_k;
+    c.pool_v = reinterpret_cast<uint32_t*>(b + l.pool_v);
+    c.lsd_tiles_a = l.lsd_tiles_a;
+    c.lsd_tiles_b_cap = l.lsd_tiles_b_cap;
+    c.est_cap = l.est_cap;
+    c.est_ocap = l.est_ocap;
+  }
   return c;
 }
 
@@ -192,12 +240,17 @@ size_t workspace_bytes(uint64_t ntot, uint32_t narr) {
 
 // Persistent grid sizes of every kernel of one key type on one device.
 struct Grids {
-  int rc, rcl, lc, sc, cl, cs, ws, cp, kf;
+  int rc, rcl, lc, sc, cl, cs, ws, cp, kf, lp, le, rc2, lp1;
 };
 
 // The tuning entry's CTAs-per-SM caps applied to the persistent grids.
 inline void apply_tune(const dfr_tune_t& t, int sms, Grids* g) {
-  if (t.scatter_ctas_per_sm && sms > 0) g->sc = std::min(g->sc, (int)t.scatter_ctas_per_sm * sms);
+  if (t.scatter_ctas_per_sm && sms > 0) {
+    g->sc = std::min(g->sc, (int)t.scatter_ctas_per_sm * sms);
+    g->lp = std::min(g->lp, (int)t.scatter_ctas_per_sm * sms);
+    g->le = std::min(g->le, (int)t.scatter_ctas_per_sm * sms);
+    g->lp1 = std::min(g->lp1, (int)t.scatter_ctas_per_sm * sms);
+  }
   if (t.ctasort_ctas_per_sm && sms > 0) g->cs = std::min(g->cs, (int)t.ctasort_ctas_per_sm * sms);
 }
 
@@ -225,9 +278,11 @@ struct Kernels {
   static constexpr size_t sc_smem = scatter_smem_bytes<K, V, SNT, SKPT>();
   static constexpr size_t cs_smem = ctasort_smem_bytes<K, V, CNT, CKPT>();
   static constexpr size_t ws_smem = (size_t)WPB * warpsort_warp_bytes<K, V, WKPT>();
+  static constexpr size_t lp_smem = lsd_smem_bytes<K, V, SNT, SKPT>();
   static constexpr int nlev = (int)sizeof(K) + EXTRA_LEVELS;
   static_assert(nlev + 1 <= MAXLV, "control blocks for every launched level");
-  static constexpr auto root_count = k_root_count<K, SNT, TILE>;
+  static constexpr auto root_count = k_root_count<K, SNT, TILE, false>;
+  static constexpr auto root_count2 = k_root_count<K, SNT, TILE, true>;
   static constexpr auto root_classify = k_root_classify<K, V, TILE, TCTA, WCAP>;
   static constexpr auto level_count = k_level_count<K, !std::is_same<V, NoVal>::value, SNT, TILE>;
   static constexpr auto scatter = k_scatter<K, V, SNT, SKPT>;
@@ -236,6 +291,11 @@ struct Kernels {
   static constexpr auto warpsort = k_warpsort<K, V, WPB, WKPT>;
   static constexpr auto copy = k_copy<K, V, SNT, TILE>;
   static constexpr auto keyfmt = k_keyfmt<K, SNT, TILE>;
+  static constexpr auto lsd_pass0 = k_lsd_pass<K, V, SNT, SKPT, 0, false>;
+  static constexpr auto lsd_est = k_lsd_pass<K, V, SNT, SKPT, 0, true>;
+  static constexpr auto lsd_pass1 = k_lsd_pass<K, V, SNT, SKPT, 1, false>;
+  static constexpr auto lsd_mid = k_lsd_mid<K, V, TILE>;
+  static constexpr auto lsd_fin = k_lsd_fin<K>;
 
   // grid_of(kernel, threads, dynamic smem) -> persistent grid (or < 0 on error)
   template <class G>
@@ -249,27 +309,64 @@ struct Kernels {
     g->ws = grid_of((const void*)warpsort, WPB * 32, ws_smem);
     g->cp = grid_of((const void*)copy, SNT, (size_t)0);
     g->kf = grid_of((const void*)keyfmt, SNT, (size_t)0);
+    g->lp = grid_of((const void*)lsd_pass0, SNT, lp_smem);
+    g->lp1 = grid_of((const void*)lsd_pass1, SNT, lp_smem);
+    g->le = grid_of((const void*)lsd_est, SNT, lp_smem);
+    g->rc2 = grid_of((const void*)root_count2, SNT, (size_t)0);
     return g->rc > 0 && g->rcl > 0 && g->lc > 0 && g->sc > 0 && g->cl > 0 && g->cs > 0 && g->ws > 0 && g->cp > 0 &&
-           g->kf > 0;
+           g->kf > 0 && g->lp > 0 && g->le > 0 && g->rc2 > 0 && g->lp1 > 0;
   }
 };
 
 inline uint32_t min_u32(uint32_t a, uint32_t b) { return a < b ? a : b; }
 
+// The schedule of a call: the plan's LSD mode for a single array large
+// enough to have the LSD workspace, the MSD schedule (0) otherwise.
+inline uint32_t lsd_mode_of(const dfr_tune_t& t, const Layout& lay, uint32_t narr) {
+  return (narr == 1u && lay.has_lsd && t.schedule <= 2u) ? t.schedule : 0u;
+}
+
 // The whole device launch sequence of one call (no host synchronisation, no
 // allocation).  `hook(kind, stream, launch_fn)` wraps every launch (profiling
 // and launch counting in the regular path, counting only in the no-allocation
-// path).  `a0` rides in k_init's parameters when `write_a0`.
+// path).  `a0` rides in k_init's parameters when `write_a0`.  With c.lsd_mode
+// set the top two digits go through the LSD phase (dfr_lsd.cuh): mode 1 =
+// root count (both digits) -> plan -> root classify -> pass 0 -> pass 1;
+// mode 2 = estimated pass 0 -> plan -> root count (skipped when the estimate
+// held) -> root classify -> pass 1.  The MSD levels follow either way.
 template <class K, class V, class Hook>
 void enqueue_sort(const Ctx& c, const Layout& lay, const Grids& g, uint32_t narr, uint32_t root_tiles,
                   unsigned long long ntot, const ArrDesc& a0, bool write_a0, cudaStream_t st, Hook&& hook) {
   using T = Kernels<K, V>;
+  const uint32_t mode = c.lsd_mode;
   const uint32_t root_words = (uint32_t)((size_t)narr * sizeof(RootAcc<K>) / 4);
   const uint32_t words = (uint32_t)(sizeof(Ctl) / 4) + root_words;
-  const uint32_t gi = min_u32((words + 255) / 256, 1024u);
-  hook(PK_INIT, st, [&] { k_init<K><<<gi, 256, 0, st>>>(c, a0, write_a0 ? 1 : 0, root_words); });
-  hook(PK_ROOT_COUNT, st, [&] { T::root_count<<<min_u32(root_tiles, (uint32_t)g.rc), T::SNT, 0, st>>>(c, root_tiles); });
+  const uint32_t z16 = mode ? lay.lsd_zero16 : 0u;
+  const uint32_t gi = min_u32((std::max(words, z16) + 255) / 256, 1024u);
+  uint4* z = mode ? reinterpret_cast<uint4*>(c.lsd) : nullptr;
+  hook(PK_INIT, st, [&] { k_init<K><<<gi, 256, 0, st>>>(c, a0, write_a0 ? 1 : 0, root_words, z, z16); });
+  const uint32_t lp_grid = min_u32(lay.lsd_tiles_a, (uint32_t)g.lp);
+  if (mode == 2u) {
+    const uint32_t le_grid = min_u32(lay.lsd_tiles_a, (uint32_t)g.le);
+    hook(PK_LSD_PASS, st, [&] { T::lsd_est<<<le_grid, T::SNT, T::lp_smem, st>>>(c); });
+    hook(PK_LSD_PLAN, st, [&] { T::lsd_mid<<<1, 256, 0, st>>>(c); });
+  }
+  if (mode == 1u) {
+    uint32_t* h2 = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(c.lsd) + offsetof(LsdCtl, h1));
+    hook(PK_ROOT_COUNT, st,
+         [&] { T::root_count2<<<min_u32(root_tiles, (uint32_t)g.rc2), T::SNT, 0, st>>>(c, root_tiles, h2); });
+  } else {
+    hook(PK_ROOT_COUNT, st,
+         [&] { T::root_count<<<min_u32(root_tiles, (uint32_t)g.rc), T::SNT, 0, st>>>(c, root_tiles, nullptr); });
+  }
+  if (mode == 1u) hook(PK_LSD_PLAN, st, [&] { T::lsd_mid<<<1, 256, 0, st>>>(c); });
   hook(PK_ROOT_CLASSIFY, st, [&] { T::root_classify<<<min_u32(narr, (uint32_t)g.rcl), 256, 0, st>>>(c, ntot); });
+  if (mode == 1u) hook(PK_LSD_PASS, st, [&] { T::lsd_pass0<<<lp_grid, T::SNT, T::lp_smem, st>>>(c); });
+  if (mode) {
+    const uint32_t lp1_grid = min_u32(lay.lsd_tiles_b_cap, (uint32_t)g.lp1);
+    hook(PK_LSD_PASS, st, [&] { T::lsd_pass1<<<lp1_grid, T::SNT, T::lp_smem, st>>>(c); });
+    hook(PK_LSD_PLAN, st, [&] { T::lsd_fin<<<M, M, 0, st>>>(c); });
+  }
   const uint32_t lc_grid = min_u32(lay.tilecap, (uint32_t)g.lc);
   const uint32_t sc_grid = min_u32(lay.tilecap, (uint32_t)g.sc);
   const uint32_t cl_grid = min_u32(lay.segcap, (uint32_t)g.cl);
@@ -310,6 +407,7 @@ int run_sort(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws
   c.nlev = (uint32_t)T::nlev;
   const dfr_tune_t tune = rt_tune(key_type_of<K, V>(), ntot / narr);
   ctx_plan<K, V>(&c, tune);
+  c.lsd_mode = lsd_mode_of(tune, lay, narr);
 
   Grids g;
   if (!T::grids([](const void* k, int t, size_t sm) { return rt_grid(k, t, sm); }, &g)) return DFR_ERR_CUDA;
@@ -368,6 +466,7 @@ int build_graph(const HostArr* arrs, uint32_t narr, void* ws, size_t ws_bytes, c
   c.nlev = (uint32_t)T::nlev;
   const dfr_tune_t tune = rt_tune(key_type_of<K, V>(), ntot / narr);
   ctx_plan<K, V>(&c, tune);
+  c.lsd_mode = lsd_mode_of(tune, lay, narr);
   Grids g;
   if (!T::grids([](const void* k, int t, size_t sm) { return rt_grid(k, t, sm); }, &g)) return DFR_ERR_CUDA;
   apply_tune(tune, rt_sms(), &g);

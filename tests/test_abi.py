@@ -121,12 +121,13 @@ def test_tune_table_api(lib):
             assert dfr.DFR_TUNE_WARP_MIN <= t["warp_max"] <= dfr.DFR_TUNE_WARP_MAX
     base = dfr.dfr_tune_get(dfr.DFR_U32, 3)
     try:
-        new = dict(base, target_log2=9, max_bits=6, warp_max=256, scatter_ctas_per_sm=1, ctasort_ctas_per_sm=1)
+        new = dict(base, target_log2=9, max_bits=6, warp_max=256, scatter_ctas_per_sm=1, ctasort_ctas_per_sm=1,
+                   schedule=dfr.DFR_SCHED_DFR)
         assert dfr.dfr_tune_set(dfr.DFR_U32, 3, new) == dfr.DFR_OK
         assert dfr.dfr_tune_get(dfr.DFR_U32, 3) == new
         for bad in (dict(base, target_log2=5), dict(base, target_log2=14), dict(base, max_bits=3),
                     dict(base, max_bits=9), dict(base, warp_max=64), dict(base, warp_max=1024),
-                    dict(base, scatter_ctas_per_sm=5)):
+                    dict(base, scatter_ctas_per_sm=5), dict(base, schedule=3)):
             assert dfr.dfr_tune_set(dfr.DFR_U32, 3, bad) == dfr.DFR_ERR_INVALID_ARG
         assert dfr.dfr_tune_set(7, 3, base) == dfr.DFR_ERR_INVALID_ARG
         assert dfr.dfr_tune_set(dfr.DFR_U32, dfr.DFR_TUNE_CLASSES, base) == dfr.DFR_ERR_INVALID_ARG
@@ -141,14 +142,17 @@ def test_tuner_writes_a_table_the_library_compiles(tmp_path):
     from paper_2207_14334_gb300 import tune
 
     table = {"DFR_U32": {"3": dict(target_log2=11, max_bits=7, warp_max=256, scatter_ctas_per_sm=2,
-                                   ctasort_ctas_per_sm=1)}}
+                                   ctasort_ctas_per_sm=1),
+                         "9": dict(target_log2=12, max_bits=8, warp_max=512, scatter_ctas_per_sm=0,
+                                   ctasort_ctas_per_sm=0, schedule=2)}}
     p = tmp_path / "t.inc"
     tune.write_inc(table, path=str(p), note="test")
     body = "".join(l for l in p.read_text().splitlines(True) if not l.startswith("//"))
-    assert body.count("{0, 0, 0}") == 4 * dfr.DFR_TUNE_CLASSES
-    assert "{11, 7, 256, 2, 1, {0, 0, 0}}" in body
+    assert body.count("{0, 0}}") == 4 * dfr.DFR_TUNE_CLASSES
+    assert "{11, 7, 256, 2, 1, 0, {0, 0}}" in body
+    assert "{12, 8, 512, 0, 0, 2, {0, 0}}" in body
     shipped = open(tune.INC).read()
-    assert "".join(l for l in shipped.splitlines(True) if not l.startswith("//")).count("{0, 0, 0}") == \
+    assert "".join(l for l in shipped.splitlines(True) if not l.startswith("//")).count("{0, 0}}") == \
         4 * dfr.DFR_TUNE_CLASSES
 
 
@@ -174,5 +178,5 @@ def test_key_format_host_checks(lib):
     assert dfr.dfr_sort_batch_format([], dfr.DFR_FMT_FLOAT | dfr.DFR_FMT_DESCENDING, 0, 0, stream=0) == dfr.DFR_OK
     # n <= 1 is a no-op in every format
     assert dfr.dfr_sort_format(dfr.DFR_U64, dfr.DFR_FMT_SIGNED, 0x1000, 0, 0x2000, 0, 1, 0, 0, stream=0) == dfr.DFR_OK
-    assert dfr.dfr_profile_kind_name if hasattr(dfr, "dfr_profile_kind_name") else True
-    assert lib.dfr_profile_kind_name(dfr.DFR_PROFILE_KINDS - 1) == b"keyfmt"
+    names = [lib.dfr_profile_kind_name(i) for i in range(dfr.DFR_PROFILE_KINDS)]
+    assert names[-3:] == [b"keyfmt", b"lsd_pass", b"lsd_plan"]
