@@ -989,10 +989,14 @@ __device__ __forceinline__ uint32_t look_back(const Ctx& c, uint32_t* status, ui
 // HBM.
 // Key-only: one returning shared atomic per key on block-wide counters gives
 // each key a distinct slot of its digit (order among equal digits is free;
-// lanes hitting one counter are serialised by the hardware, which measured
-// cheaper than aggregating them in software even on skewed inputs); the tile
-// claims its run of every bucket with one atomic on the bucket's fill cursor;
-// full tiles of 16-byte-aligned arrays are read with 128-bit loads.
+// lanes hitting one counter are serialised by the hardware).  A tile that
+// follows one with at most RUN_DIGITS distinct digits in the same CTA (runs
+// of equal digits: sorted or reverse-sorted input, heavy values) first checks
+// each warp's 32 x VK consecutive keys: if they all share a digit the warp
+// takes their slots with a single atomic.  Other tiles skip that check, which
+// costs more than it saves on random digits.  The tile claims its run of
+// every bucket with one atomic on the bucket's fill cursor; full tiles of
+// 16-byte-aligned arrays are read with 128-bit loads.
 // Key-value: stable per-warp ranking in element order, tiles placed in tile
 // order by a single-pass decoupled look-back per digit.
 template <class K, class V, int NT, int KPT>
@@ -1010,6 +1014,8 @@ __global__ void __launch_bounds__(NT, (std::is_same<V, NoVal>::value ? 3 : 2)) k
   uint32_t* s_goff = s_tstart + M;  // global destination of staged element e of digit d = s_goff[d] + e
   __shared__ uint32_t s_scan[16];
   __shared__ uint32_t s_t, s_fail;
+  __shared__ uint32_t s_run, s_nd;  // key-only: run mode for this tile; distinct digits of the last one
+  constexpr uint32_t RUN_DIGITS = 8;
 
   LevelCtl* lc = &c.ctl->lv[L];
   const uint32_t ntiles = min(lc->ntiles, c.tilecap);
@@ -1018,12 +1024,15 @@ __global__ void __launch_bounds__(NT, (std::is_same<V, NoVal>::value ? 3 : 2)) k
   uint32_t* cur = ((L & 1) ? c.cur[1] : c.cur[0]);
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
 
+  if (threadIdx.x == 0) s_nd = M;
   // Tiles are claimed in increasing order by running CTAs only, so the tile a
   // look-back waits for is always being processed by some resident CTA.
   for (;;) {
     if (threadIdx.x == 0) {
       s_t = atomicAdd(&lc->scat_claim, 1u);
       s_fail = 0u;
+      s_run = s_nd <= RUN_DIGITS ? 1u : 0u;
+      s_nd = 0u;
     }
     for (uint32_t i = threadIdx.x; i < (uint32_t)(KV ? NW * M : M); i += NT) s_cnt[i] = 0u;
     __syncthreads();
@@ -1096,10 +1105,41 @@ __global__ void __launch_bounds__(NT, (std::is_same<V, NoVal>::value ? 3 : 2)) k
           k[i] = (e >= vlo && e < vhi) ? src[tb + e] : K(0);
         }
       }
+      if (s_run) {
+        // chunk q of a warp = its lanes' items VK*q .. VK*q+VK-1: 32 x VK
+        // consecutive keys, lane 0 holding the first and lane 31 the last
 #pragma unroll
-      for (int i = 0; i < KPT; ++i) {
-        const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
-        r[i] = (e >= vlo && e < vhi) ? atomicAdd(&s_cnt[digit_of(k[i], shift)], 1u) : 0u;
+        for (int q = 0; q < KPT / (int)VK; ++q) {
+          const uint32_t e0 = VK * ((uint32_t)q * NT + threadIdx.x);
+          const uint32_t dfirst = __shfl_sync(FULL, digit_of(k[q * VK], shift), 0);
+          const uint32_t dlast = __shfl_sync(FULL, digit_of(k[q * VK + VK - 1], shift), 31);
+          bool one = false;
+          if (dfirst == dlast) {
+            bool mine = e0 >= vlo && e0 + VK <= vhi;
+#pragma unroll
+            for (int u = 0; u < (int)VK; ++u) mine = mine && digit_of(k[q * VK + u], shift) == dfirst;
+            one = __all_sync(FULL, mine);
+          }
+          if (one) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&s_cnt[dfirst], 32u * VK);
+            base = __shfl_sync(FULL, base, 0) + lane * VK;
+#pragma unroll
+            for (int u = 0; u < (int)VK; ++u) r[q * VK + u] = base + (uint32_t)u;
+          } else {
+#pragma unroll
+            for (int u = 0; u < (int)VK; ++u) {
+              const uint32_t e = e0 + (uint32_t)u;
+              r[q * VK + u] = (e >= vlo && e < vhi) ? atomicAdd(&s_cnt[digit_of(k[q * VK + u], shift)], 1u) : 0u;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < KPT; ++i) {
+          const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
+          r[i] = (e >= vlo && e < vhi) ? atomicAdd(&s_cnt[digit_of(k[i], shift)], 1u) : 0u;
+        }
       }
     }
     __syncthreads();
@@ -1117,6 +1157,10 @@ __global__ void __launch_bounds__(NT, (std::is_same<V, NoVal>::value ? 3 : 2)) k
         tcount = s_cnt[threadIdx.x];
       }
       if constexpr (KV) st_relaxed(c.status + (size_t)t * M + threadIdx.x, (j == 0 ? FLAG_INC : FLAG_AGG) | tcount);
+      if constexpr (!KV) {
+        const uint32_t nd = __reduce_add_sync(FULL, tcount ? 1u : 0u);  // (read after the next barrier)
+        if (lane == 0 && nd) atomicAdd(&s_nd, nd);
+      }
     }
     const uint32_t hcount = threadIdx.x < M ? hist[(size_t)s * M + threadIdx.x] : 0u;
     uint32_t tstart, bexcl;

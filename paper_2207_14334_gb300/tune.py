@@ -8,6 +8,9 @@ every candidate plan, times each with CUDA events (inputs restored and L2
 flushed before every repetition, outside the timed region), and keeps the
 fastest.  The plans never change a result, only the time.
 
+For single arrays of at least dfr_lsd_min_keys keys it also tries the LSD
+schedule of the top digits (Algorithm 4) on top of the best MSD plan.
+
 Writes the table as JSON and as the C include compiled into the library
 (csrc/dfr_tune_table.inc); rebuild afterwards.  Needs a GPU:
 
@@ -36,13 +39,14 @@ def class_length(c: int) -> int:
 
 
 def candidates(cap_log2: int):
-    """The plan grid searched for one (key type, class)."""
+    """The plan grid searched for one (key type, class) with the MSD schedule."""
     out = []
     for tl, mb, wm, sc, cs in itertools.product((cap_log2 - 2, cap_log2 - 1, cap_log2), (8, 7), (128, 256, 512),
                                                 (0, 2), (0, 1)):
         if mb == 7 and (sc, cs) != (0, 0):
             continue  # narrower windows are tried with the default grids only
-        out.append(dict(target_log2=tl, max_bits=mb, warp_max=wm, scatter_ctas_per_sm=sc, ctasort_ctas_per_sm=cs))
+        out.append(dict(target_log2=tl, max_bits=mb, warp_max=wm, scatter_ctas_per_sm=sc, ctasort_ctas_per_sm=cs,
+                        schedule=0))
     return out
 
 
@@ -94,7 +98,7 @@ class Case:
         return ts[len(ts) // 2]
 
 
-def tune(key_types, classes, reps: int, budget_keys: int, log=print):
+def tune(key_types, classes, reps: int, budget_keys: int, schedules=(0, 1), log=print):
     import torch
 
     import paper_2207_14334_gb300 as dfr
@@ -115,6 +119,18 @@ def tune(key_types, classes, reps: int, budget_keys: int, log=print):
                 ms = case.time_ms(reps)
                 if best is None or ms < best[0]:
                     best = (ms, plan)
+            # The schedule of the top digits applies to single arrays large
+            # enough for the LSD phase: tried on top of the best MSD plan.
+            if count == 1 and n >= dfr.dfr_lsd_min_keys(kt):
+                for sched in schedules:
+                    if sched == 0:
+                        continue
+                    plan = dict(best[1], schedule=sched)
+                    dfr.check(dfr.dfr_tune_set(kt, c, plan), "tune_set")
+                    case.time_ms(2)
+                    ms = case.time_ms(reps)
+                    if ms < best[0]:
+                        best = (ms, plan)
             dfr.dfr_tune_reset()
             default_ms = case.time_ms(reps)
             table.setdefault(ktn, {})[str(c)] = dict(best[1], ms=best[0], default_ms=default_ms, n=n, arrays=count)
@@ -154,11 +170,15 @@ def main(argv=None):
     ap.add_argument("--out-json", default="")
     ap.add_argument("--write-inc", action="store_true")
     ap.add_argument("--inc-path", default=INC)
+    ap.add_argument("--schedules", default="0,1",
+                    help="schedules of the top digits to try on single large arrays (0 MSD, 1 LSD, 2 LSD with the "
+                         "estimated deal, which falls back to MSD on skewed inputs and is left out by default)")
     args = ap.parse_args(argv)
     if os.path.dirname(HERE) not in sys.path:
         sys.path.insert(0, os.path.dirname(HERE))
     t0 = time.time()
-    table = tune(args.key_types.split(","), [int(x) for x in args.classes.split(",")], args.reps, args.budget_keys)
+    table = tune(args.key_types.split(","), [int(x) for x in args.classes.split(",")], args.reps, args.budget_keys,
+                 schedules=tuple(int(x) for x in args.schedules.split(",")))
     import torch
 
     meta = {"device": torch.cuda.get_device_name(0), "date": datetime.date.today().isoformat(),
