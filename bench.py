@@ -878,35 +878,53 @@ def main():
     kernel_share = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}
 
     # End to end through the C ABI: pinned host keys -> device -> sort -> host.
+    # Two streams with a device buffer set each: the upload of the step's next
+    # array overlaps the sort and the download of the previous one (the two
+    # copy directions run on separate copy engines).  Every host<->device copy
+    # of the step is inside the timed region.
     e2e = None
     if not args.no_e2e:
         host_in = {d: torch.from_numpy(a.view(np.int32) if a.dtype == np.uint32 else a.view(np.int64)).pin_memory()
                    for d, a in inputs.items()}
-        host_out = torch.empty_like(next(iter(host_in.values()))).pin_memory()
+        host_out = [torch.empty_like(next(iter(host_in.values()))).pin_memory() for _ in range(2)]
         hv_in = torch.from_numpy(synth.index_payload(n).view(np.int32)).pin_memory() if kv else None
-        hv_out = torch.empty_like(hv_in).pin_memory() if kv else None
+        hv_out = [torch.empty_like(hv_in).pin_memory() for _ in range(2)] if kv else [None, None]
+        streams = [stream, torch.cuda.Stream(dev)]
+        works = [work, torch.empty_like(work)]
+        valss = [vals, torch.empty_like(vals)] if kv else [None, None]
+        sorters = [sorter, dfr.Sorter(kt, n, dev)]
         e2e_ms = []
         for step in range(max(1, min(args.steps, 3))):
-            tot = 0.0
-            for d in inputs:
-                flush.fill_(1)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                work.copy_(host_in[d], non_blocking=True)
-                if kv:
-                    vals.copy_(hv_in, non_blocking=True)
-                sorter.sort_(work, vals, n, stream)
-                host_out.copy_(work, non_blocking=True)
-                if kv:
-                    hv_out.copy_(vals, non_blocking=True)
-                e1.record(stream)
-                e1.synchronize()
-                tot += e0.elapsed_time(e1)
-            e2e_ms.append(tot)
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(streams[0])
+            streams[1].wait_event(e0)
+            for i, d in enumerate(inputs):
+                j = i % 2
+                with torch.cuda.stream(streams[j]):
+                    works[j].copy_(host_in[d], non_blocking=True)
+                    if kv:
+                        valss[j].copy_(hv_in, non_blocking=True)
+                    sorters[j].sort_(works[j], valss[j], n, streams[j])
+                    host_out[j].copy_(works[j], non_blocking=True)
+                    if kv:
+                        hv_out[j].copy_(valss[j], non_blocking=True)
+            joined = torch.cuda.Event()
+            joined.record(streams[1])
+            streams[0].wait_event(joined)
+            e1.record(streams[0])
+            e1.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+        for j in range(2):
+            st = sorters[j].device_status(streams[j])
+            if st != dfr.DFR_OK:
+                raise RuntimeError("device status %s in the end-to-end run" % dfr.dfr_status_string(st))
         ms, e2e_rate = job_rate(sum(e2e_ms) / len(e2e_ms), keys_per_step, world, dev)
         e2e = {"value": e2e_rate, "unit": "Gkeys/s",
                "h2d_bytes_per_step": keys_per_step * rec, "d2h_bytes_per_step": keys_per_step * rec,
-               "ms_per_step": ms}
+               "ms_per_step": ms, "streams": 2,
+               "overlap": "the next array's upload overlaps the previous array's sort and download"}
 
     cpu = None
     if rank == 0 and world == 1:
