@@ -954,6 +954,123 @@ __device__ __forceinline__ bool seg_is_dealt(const Seg& seg) {
   return vm != K(0) && ((vm >> seg.shift) & (K)(M - 1)) != K(0);
 }
 
+// Adaptive key-only ranking (k_scatter and the LSD passes).  One returning
+// shared atomic per key on block-wide counters gives each key a distinct slot
+// of its digit (the order among equal digits is free); lanes that hit one
+// counter are serialised by the hardware.  Two tile kinds are cheaper to rank
+// otherwise, and a CTA recognises them from the tile it dealt last:
+//  * run mode, after a tile of at most RUN_DIGITS distinct digits (runs of
+//    equal digits: sorted or reverse-sorted input, heavy values): each warp's
+//    32 x VK consecutive keys are checked first, and a chunk whose keys all
+//    share a digit takes its slots with a single atomic;
+//  * dominant-digit mode, after a tile whose most frequent digit held at
+//    least half its keys (a digit scattered at random, as the exponential's
+//    top byte or a heavy Zipf value's bucket): keys of that digit are ranked
+//    by one ballot and one atomic per warp item.
+// Other tiles skip both checks, which cost more than they save on random
+// digits.  The state lives in shared memory; thread 0 updates the modes at
+// the top of each tile, the first M threads note the tile's digit counts.
+constexpr uint32_t RUN_DIGITS = 8;
+constexpr uint32_t NO_DIGIT = 0xffffffffu;
+
+struct TileDigits {
+  uint32_t run;    // run mode for this tile
+  uint32_t dom;    // dominant digit for this tile, or NO_DIGIT
+  uint32_t nd;     // distinct digits of the tile being ranked
+  uint32_t dompk;  // max over digits of (count << 8 | digit) of the tile being ranked
+  uint32_t nvl;    // keys of the tile being ranked
+};
+
+// Thread 0, before the first tile.
+__device__ __forceinline__ void adapt_init(TileDigits& a) {
+  a.nd = M;
+  a.dompk = 0u;
+  a.nvl = 1u;
+}
+
+// Thread 0, at the top of every tile (after the previous tile's last barrier).
+__device__ __forceinline__ void adapt_next(TileDigits& a) {
+  a.run = a.nd <= RUN_DIGITS ? 1u : 0u;
+  a.dom = ((a.dompk >> 8) * 2u >= a.nvl) ? (a.dompk & 255u) : NO_DIGIT;
+  a.nd = 0u;
+  a.dompk = 0u;
+}
+
+// Threads [0, M) (whole warps), with thread d holding the tile's count of
+// digit d; read by thread 0 after the tile's last barrier.
+__device__ __forceinline__ void adapt_note(TileDigits& a, uint32_t tcount, uint32_t nvalid) {
+  const uint32_t nd = __reduce_add_sync(FULL, tcount ? 1u : 0u);
+  if (lane_id() == 0 && nd) atomicAdd(&a.nd, nd);
+  const uint32_t pk = __reduce_max_sync(FULL, (tcount << 8) | threadIdx.x);
+  if (lane_id() == 0) atomicMax(&a.dompk, pk);
+  if (threadIdx.x == 0) a.nvl = nvalid;
+}
+
+// Rank the key-only items of one tile: item i = VK*q + u of thread x is
+// element VK*(q*NT + x) + u, elements [vlo, vhi) are valid; r[i] = a
+// distinct slot of the key's digit on the counters cnt.  Every thread of the
+// block calls it.
+template <class K, int NT, int KPT>
+__device__ __forceinline__ void rank_keys(const K (&k)[KPT], uint32_t (&r)[KPT], uint32_t shift, uint32_t vlo,
+                                          uint32_t vhi, uint32_t* cnt, const TileDigits& a) {
+  constexpr uint32_t VK = 16 / sizeof(K);
+  const uint32_t lane = lane_id();
+  if (a.run) {
+    // chunk q of a warp = its lanes' items VK*q .. VK*q+VK-1: 32 x VK
+    // consecutive keys, lane 0 holding the first and lane 31 the last
+#pragma unroll
+    for (int q = 0; q < KPT / (int)VK; ++q) {
+      const uint32_t e0 = VK * ((uint32_t)q * NT + threadIdx.x);
+      const uint32_t dfirst = __shfl_sync(FULL, digit_of(k[q * VK], shift), 0);
+      const uint32_t dlast = __shfl_sync(FULL, digit_of(k[q * VK + VK - 1], shift), 31);
+      bool one = false;
+      if (dfirst == dlast) {
+        bool mine = e0 >= vlo && e0 + VK <= vhi;
+#pragma unroll
+        for (int u = 0; u < (int)VK; ++u) mine = mine && digit_of(k[q * VK + u], shift) == dfirst;
+        one = __all_sync(FULL, mine);
+      }
+      if (one) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&cnt[dfirst], 32u * VK);
+        base = __shfl_sync(FULL, base, 0) + lane * VK;
+#pragma unroll
+        for (int u = 0; u < (int)VK; ++u) r[q * VK + u] = base + (uint32_t)u;
+      } else {
+#pragma unroll
+        for (int u = 0; u < (int)VK; ++u) {
+          const uint32_t e = e0 + (uint32_t)u;
+          r[q * VK + u] = (e >= vlo && e < vhi) ? atomicAdd(&cnt[digit_of(k[q * VK + u], shift)], 1u) : 0u;
+        }
+      }
+    }
+  } else if (a.dom != NO_DIGIT) {
+    const uint32_t dom = a.dom;
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) {
+      const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
+      const bool valid = e >= vlo && e < vhi;
+      const uint32_t d = digit_of(k[i], shift);
+      const bool isdom = valid && d == dom;
+      const uint32_t m = __ballot_sync(FULL, isdom);
+      uint32_t base = 0;
+      if (m) {
+        const int leader = __ffs((int)m) - 1;
+        if ((int)lane == leader) base = atomicAdd(&cnt[dom], (uint32_t)__popc(m));
+        base = __shfl_sync(FULL, base, leader);
+      }
+      r[i] = isdom ? base + (uint32_t)__popc(m & lt) : (valid ? atomicAdd(&cnt[d], 1u) : 0u);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) {
+      const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
+      r[i] = (e >= vlo && e < vhi) ? atomicAdd(&cnt[digit_of(k[i], shift)], 1u) : 0u;
+    }
+  }
+}
+
 // Decoupled look-back for digit d of tile t (one thread per digit): sums the
 // counts of the earlier tiles of the segment back to the first inclusive
 // prefix, then publishes this tile's inclusive prefix.  Every wait is bounded
@@ -995,16 +1112,11 @@ __device__ __forceinline__ uint32_t look_back(const Ctx& c, uint32_t* status, ui
 // shared memory, placed inside each bucket of its segment, staged in digit
 // order and written to the other buffer, so each digit's run is contiguous in
 // HBM.
-// Key-only: one returning shared atomic per key on block-wide counters gives
-// each key a distinct slot of its digit (order among equal digits is free;
-// lanes hitting one counter are serialised by the hardware).  A tile that
-// follows one with at most RUN_DIGITS distinct digits in the same CTA (runs
-// of equal digits: sorted or reverse-sorted input, heavy values) first checks
-// each warp's 32 x VK consecutive keys: if they all share a digit the warp
-// takes their slots with a single atomic.  Other tiles skip that check, which
-// costs more than it saves on random digits.  The tile claims its run of
-// every bucket with one atomic on the bucket's fill cursor; full tiles of
-// 16-byte-aligned arrays are read with 128-bit loads.
+// Key-only: adaptive ranking (rank_keys: one shared atomic per key, one per
+// warp run of a digit, or one ballot per warp item for a dominant digit);
+// the tile claims its run of every bucket with one atomic on the bucket's
+// fill cursor; full tiles of 16-byte-aligned arrays are read with 128-bit
+// loads.
 // Key-value: stable per-warp ranking in element order, tiles placed in tile
 // order by a single-pass decoupled look-back per digit.
 template <class K, class V, int NT, int KPT>
@@ -1022,8 +1134,7 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false>())) k_s
   uint32_t* s_goff = s_tstart + M;  // global destination of staged element e of digit d = s_goff[d] + e
   __shared__ uint32_t s_scan[16];
   __shared__ uint32_t s_t, s_fail;
-  __shared__ uint32_t s_run, s_nd;  // key-only: run mode for this tile; distinct digits of the last one
-  constexpr uint32_t RUN_DIGITS = 8;
+  __shared__ TileDigits s_ad;  // key-only adaptive ranking state
 
   LevelCtl* lc = &c.ctl->lv[L];
   const uint32_t ntiles = min(lc->ntiles, c.tilecap);
@@ -1032,15 +1143,14 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false>())) k_s
   uint32_t* cur = ((L & 1) ? c.cur[1] : c.cur[0]);
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
 
-  if (threadIdx.x == 0) s_nd = M;
+  if (threadIdx.x == 0) adapt_init(s_ad);
   // Tiles are claimed in increasing order by running CTAs only, so the tile a
   // look-back waits for is always being processed by some resident CTA.
   for (;;) {
     if (threadIdx.x == 0) {
       s_t = atomicAdd(&lc->scat_claim, 1u);
       s_fail = 0u;
-      s_run = s_nd <= RUN_DIGITS ? 1u : 0u;
-      s_nd = 0u;
+      adapt_next(s_ad);
     }
     for (uint32_t i = threadIdx.x; i < (uint32_t)(KV ? NW * M : M); i += NT) s_cnt[i] = 0u;
     __syncthreads();
@@ -1113,42 +1223,7 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false>())) k_s
           k[i] = (e >= vlo && e < vhi) ? src[tb + e] : K(0);
         }
       }
-      if (s_run) {
-        // chunk q of a warp = its lanes' items VK*q .. VK*q+VK-1: 32 x VK
-        // consecutive keys, lane 0 holding the first and lane 31 the last
-#pragma unroll
-        for (int q = 0; q < KPT / (int)VK; ++q) {
-          const uint32_t e0 = VK * ((uint32_t)q * NT + threadIdx.x);
-          const uint32_t dfirst = __shfl_sync(FULL, digit_of(k[q * VK], shift), 0);
-          const uint32_t dlast = __shfl_sync(FULL, digit_of(k[q * VK + VK - 1], shift), 31);
-          bool one = false;
-          if (dfirst == dlast) {
-            bool mine = e0 >= vlo && e0 + VK <= vhi;
-#pragma unroll
-            for (int u = 0; u < (int)VK; ++u) mine = mine && digit_of(k[q * VK + u], shift) == dfirst;
-            one = __all_sync(FULL, mine);
-          }
-          if (one) {
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&s_cnt[dfirst], 32u * VK);
-            base = __shfl_sync(FULL, base, 0) + lane * VK;
-#pragma unroll
-            for (int u = 0; u < (int)VK; ++u) r[q * VK + u] = base + (uint32_t)u;
-          } else {
-#pragma unroll
-            for (int u = 0; u < (int)VK; ++u) {
-              const uint32_t e = e0 + (uint32_t)u;
-              r[q * VK + u] = (e >= vlo && e < vhi) ? atomicAdd(&s_cnt[digit_of(k[q * VK + u], shift)], 1u) : 0u;
-            }
-          }
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < KPT; ++i) {
-          const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
-          r[i] = (e >= vlo && e < vhi) ? atomicAdd(&s_cnt[digit_of(k[i], shift)], 1u) : 0u;
-        }
-      }
+      rank_keys<K, NT, KPT>(k, r, shift, vlo, vhi, s_cnt, s_ad);
     }
     __syncthreads();
 
@@ -1165,10 +1240,7 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false>())) k_s
         tcount = s_cnt[threadIdx.x];
       }
       if constexpr (KV) st_relaxed(c.status + (size_t)t * M + threadIdx.x, (j == 0 ? FLAG_INC : FLAG_AGG) | tcount);
-      if constexpr (!KV) {
-        const uint32_t nd = __reduce_add_sync(FULL, tcount ? 1u : 0u);  // (read after the next barrier)
-        if (lane == 0 && nd) atomicAdd(&s_nd, nd);
-      }
+      if constexpr (!KV) adapt_note(s_ad, tcount, nvalid);
     }
     const uint32_t hcount = threadIdx.x < M ? hist[(size_t)s * M + threadIdx.x] : 0u;
     uint32_t tstart, bexcl;

@@ -37,7 +37,7 @@
 //
 // Ordering: key-value sorts rank stably inside a tile and chain tiles in
 // tile order in both passes (payloads keep input order on ties).  Key-only
-// sorts rank with block-wide shared atomics; pass 0 claims its bucket space
+// sorts rank with the scatter's adaptive ranking (rank_keys); pass 0 claims its bucket space
 // with fill-cursor atomics (the order inside a D1 bucket is free: every
 // prefix bucket is sorted afterwards), pass 1 keeps the look-back because the
 // D1 buckets must stay in order inside every D0 bucket.
@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, EST>())) k_lsd
   uint32_t* s_h0 = s_ovf + M;      // estimated pass: D0 counts of this CTA's tiles
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_t, s_fail, s_p;
+  __shared__ TileDigits s_ad;  // key-only adaptive ranking state
 
   LsdCtl* lsd = c.lsd;
   constexpr bool est = EST;
@@ -95,9 +96,11 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, EST>())) k_lsd
     for (uint32_t i = threadIdx.x; i < (uint32_t)M; i += NT) s_h0[i] = 0u;
   K orv = 0, nandv = 0;
   unsigned long long dealt = 0;
+  if (threadIdx.x == 0) adapt_init(s_ad);
 
   for (;;) {
     if (threadIdx.x == 0) {
+      adapt_next(s_ad);
       uint32_t t = ntiles;
       // after a failed estimate no new tile is claimed (tiles already claimed
       // finish, so no look-back waits on a tile nobody processes)
@@ -199,15 +202,16 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, EST>())) k_lsd
           k[i] = (e >= vlo && e < vhi) ? src[tb + e] : K(0);
         }
       }
+      rank_keys<K, NT, KPT>(k, r, shift, vlo, vhi, s_cnt, s_ad);
+      if (est) {
 #pragma unroll
-      for (int i = 0; i < KPT; ++i) {
-        const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
-        const bool valid = e >= vlo && e < vhi;
-        r[i] = valid ? atomicAdd(&s_cnt[digit_of(k[i], shift)], 1u) : 0u;
-        if (est && valid) {
-          atomicAdd(&s_h0[digit_of(k[i], W - RB)], 1u);
-          orv |= k[i];
-          nandv |= ~k[i];
+        for (int i = 0; i < KPT; ++i) {
+          const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
+          if (e >= vlo && e < vhi) {
+            atomicAdd(&s_h0[digit_of(k[i], W - RB)], 1u);
+            orv |= k[i];
+            nandv |= ~k[i];
+          }
         }
       }
     }
@@ -228,6 +232,7 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, EST>())) k_lsd
         tcount = s_cnt[threadIdx.x];
       }
       if (chained) st_relaxed(status + (size_t)t * M + threadIdx.x, (t == 0 ? FLAG_INC : FLAG_AGG) | tcount);
+      if constexpr (!KV) adapt_note(s_ad, tcount, nvalid);
     }
     const uint32_t tstart = scan256(tcount, s_scan, nullptr);
     if (threadIdx.x < M) {

@@ -109,3 +109,20 @@ def test_u64_sorted_runs(dfr):
     b = np.repeat(synth.uniform64_u64(n // 1000 + 1, synth.BASE_SEED + 2601), 1000)[:n]
     k, _, st = gpu_sort(dfr, b)
     assert st == dfr.DFR_OK and np.array_equal(k, oracle.sort_u64(b))
+
+
+@pytest.mark.parametrize("share", [0.5, 0.7, 0.95, 0.999])
+def test_dominant_digit(dfr, share):
+    # one top byte held by a large share of the keys at random positions (the
+    # scatter's dominant-digit ranking), the rest uniform; and one heavy value
+    # inside that heavy bucket (a dominant digit again at the next level)
+    n = 2_000_011
+    g = np.random.default_rng(int(share * 1000) + 2700)
+    a = g.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
+    pick = g.random(n) < share
+    a[pick] = (a[pick] & np.uint32(0x00FFFFFF)) | np.uint32(0x5A000000)
+    _check(dfr, a)
+    heavy = g.random(n) < share * share
+    b = a.copy()
+    b[heavy] = np.uint32(0x5A3C1234)
+    _check(dfr, b)

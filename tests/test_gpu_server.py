@@ -260,3 +260,38 @@ def test_served_fifo_plain_mode(dfr, inflight):
     reqs, stats = _device_stream(dfr, 120, 52, 1 << 6, 1 << 18, max_batch=1, n_streams=1, inflight=inflight)
     assert stats["batches"] == len(reqs)
     _check_stream(dfr, reqs)
+
+
+@pytest.mark.parametrize("sched", [1, 2])
+def test_served_single_large_request_lsd_schedule(dfr, sched):
+    """A request served alone (a batch of one array) takes the plan's schedule
+    of the top digits: with the LSD schedules forced, large u64 key-value and
+    u32 requests still come out as the oracle sorts them."""
+    import torch
+
+    try:
+        for kt in (dfr.DFR_U64_KV, dfr.DFR_U32):
+            for c in range(dfr.DFR_TUNE_CLASSES):
+                t = dfr.dfr_tune_get(kt, c)
+                t["schedule"] = sched
+                assert dfr.dfr_tune_set(kt, c, t) == dfr.DFR_OK
+        reqs = [_Req(dfr, dfr.DFR_U64_KV, *_make(dfr, dfr.DFR_U64_KV, (1 << 21) + 5, synth.BASE_SEED + 810), False),
+                _Req(dfr, dfr.DFR_U32, *_make(dfr, dfr.DFR_U32, (1 << 21) + 77, synth.BASE_SEED + 811), True)]
+        torch.cuda.synchronize()
+        srv = dfr.dfr_server_create(torch.cuda.current_device(), 512 << 20, 1)
+        try:
+            for r in reqs:  # one at a time: each runs as a batch of one
+                rc, t = dfr.dfr_submit(srv, r.seg())
+                assert rc == dfr.DFR_OK
+                rc, _ = dfr.dfr_wait(srv, t)
+                assert rc == dfr.DFR_OK
+        finally:
+            assert dfr.dfr_server_destroy(srv) == dfr.DFR_OK
+    finally:
+        assert dfr.dfr_tune_reset() == dfr.DFR_OK
+    for r in reqs:
+        k, v = r.result(dfr)
+        ek, ev = _expected(r.kt, r.a, r.v)
+        assert np.array_equal(k, ek)
+        if ev is not None:
+            assert np.array_equal(v, ev)
