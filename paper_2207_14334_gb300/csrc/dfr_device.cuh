@@ -1609,7 +1609,9 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
 //    groups hold equal keys and the bucket is sorted, otherwise each key is
 //    placed inside its (small) group by the rank an insertion sort would give
 //    it (keys below it, plus equal keys stored before it).  A group of more
-//    than GMAX keys (skewed bucket) falls back to the LSD passes.
+//    than GMAX keys (skewed bucket) keeps its staged order if it holds one
+//    repeated key; a bucket with a larger group of mixed keys falls back to
+//    the LSD passes.
 //  * Otherwise: an LSD radix sort in shared memory over the bucket's varying
 //    bits only (windows of RB bits, constant bits skipped); every pass is
 //    stable except the first of a key-only sort.
@@ -1652,7 +1654,7 @@ template <class K, class V, int NT, int KPT, int KPTA>
 __device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const uint32_t* vsrc, K* dst, uint32_t* vdst,
                                                 uint32_t off, uint32_t len, bool par, K* s_keys, uint32_t* s_vals,
                                                 uint32_t* s_whist, uint32_t* s_dstart, uint32_t* s_scan,
-                                                uint32_t* s_scan16, uint32_t* s_maxc,
+                                                uint32_t* s_scan16, uint32_t* s_maxc, uint32_t* s_mixed,
                                                 unsigned long long* s_orv, K* s_out, uint16_t* s_pos,
                                                 uint16_t* s_perm) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
@@ -1838,6 +1840,55 @@ __device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const ui
       }
       return;
     }
+    if (!KV && span > wbits) {
+      // Some group holds more than GMAX keys.  If every such group holds one
+      // repeated key (a heavy value, as in Zipf buckets), its keys need no
+      // order and keep their staged slots, and the other groups take the
+      // insertion rank; if one of them mixes keys, fall back to LSD.
+      if (threadIdx.x == 0) *s_mixed = 0u;
+#pragma unroll
+      for (int i = 0; i < KPTA; ++i) {
+        if ((uint32_t)(i * 32) + lane < wvalid) {
+          const uint32_t pos = cnt[(uint32_t)(k[i] >> gshift) & (nb - 1u)] + r[i];
+          if (pos < len)
+            s_keys[pos] = k[i];
+          else
+            record_error(ctl, DERR_BOUNDS, ERR_SITE_CTASORT_STAGE);
+        }
+      }
+      __syncthreads();
+      for (uint32_t e = threadIdx.x; e < len; e += NT) {
+        const K key = s_keys[e];
+        const uint32_t h = (uint32_t)(key >> gshift) & (nb - 1u);
+        const uint32_t gs = cnt[h];
+        const uint32_t ge = h + 1u < nb ? cnt[h + 1u] : len;
+        if (ge - gs > GMAX && key != s_keys[gs]) *s_mixed = 1u;
+      }
+      __syncthreads();
+      if (*s_mixed == 0u) {
+        if (threadIdx.x == 0) atomicAdd(&ctl->group_buckets, 1ull);
+        const uint32_t osh = granule_shift(dst + off);
+        for (uint32_t e = threadIdx.x; e < len; e += NT) {
+          const K key = s_keys[e];
+          const uint32_t h = (uint32_t)(key >> gshift) & (nb - 1u);
+          const uint32_t gs = cnt[h];
+          const uint32_t ge = h + 1u < nb ? cnt[h + 1u] : len;
+          uint32_t slot = e;
+          if (ge - gs <= GMAX) {
+            uint32_t rank = 0;
+            for (uint32_t jj = gs; jj < ge; ++jj) {
+              const K kj = s_keys[jj];
+              rank += (kj < key || (kj == key && jj < e)) ? 1u : 0u;
+            }
+            slot = gs + rank;
+          }
+          s_out[osh + slot] = key;
+        }
+        __syncthreads();
+        store_staged<K, NT>(s_out, osh, dst + off, len);
+        return;
+      }
+    }
     // skewed bucket: LSD passes from the registers (r[] is recomputed)
   }
   uint32_t sh = (uint32_t)low_bit<K>(vm);
@@ -1921,7 +1972,7 @@ __global__ void __launch_bounds__(NT, (ctasort_min_blocks<K, V, NT>())) k_ctasor
   static_assert(!KV || CAP <= 65536u, "u16 positions");
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_scan16[NW];
-  __shared__ uint32_t s_q, s_maxc;
+  __shared__ uint32_t s_q, s_maxc, s_mixed;
   __shared__ unsigned long long s_orv[2];
   Ctl* ctl = c.ctl;
   const uint32_t count = min(ctl->cta_count, c.ctacap);
@@ -1952,7 +2003,7 @@ __global__ void __launch_bounds__(NT, (ctasort_min_blocks<K, V, NT>())) k_ctasor
       const uint32_t kpt = (len + NT - 1) / NT;  // 1..KPT keys per lane
 #define DFR_CTA_BODY(A)                                                                                      \
   cta_sort_bucket<K, V, NT, KPT, A>(ctl, src, vsrc, dst, vdst, off, len, par, s_keys, s_vals, s_whist, s_dstart, \
-                                    s_scan, s_scan16, &s_maxc, s_orv, s_out, s_pos, s_perm)
+                                    s_scan, s_scan16, &s_maxc, &s_mixed, s_orv, s_out, s_pos, s_perm)
       if (kpt <= 1)
         DFR_CTA_BODY(1);
       else if (kpt <= 2)
