@@ -1661,7 +1661,7 @@ __device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const ui
   constexpr int NW = NT / 32;
   constexpr int W = 8 * sizeof(K);
   constexpr int GB = (NW * M >= 8192) ? 13 : (NW * M >= 4096) ? 12 : (NW * M >= 2048 ? 11 : 10);
-  constexpr uint32_t GMAX = 32;
+  constexpr uint32_t GMAX = 64;  // largest group ranked by the in-group insertion rank (measured: 32 or 48 slower on Zipf)
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   uint32_t* wh = s_whist + warp * M;
   const uint32_t wb = warp * 32u * KPTA;
@@ -1723,8 +1723,13 @@ __device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const ui
     if (threadIdx.x == 0) *s_maxc = 0u;
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < KPTA; ++i)
-      r[i] = ((uint32_t)(i * 32) + lane < wvalid) ? atomicAdd(&cnt[(uint32_t)(k[i] >> gshift) & (nb - 1u)], 1u) : 0u;
+    for (int i = 0; i < KPTA; ++i) {
+      const uint32_t ri = ((uint32_t)(i * 32) + lane < wvalid) ? atomicAdd(&cnt[(uint32_t)(k[i] >> gshift) & (nb - 1u)], 1u) : 0u;
+      if constexpr (KV)
+        r[i] = ri;
+      else
+        s_out[(uint32_t)i * NT + threadIdx.x] = (K)ri;  // parked in the idle output buffer until staging (fewer live registers)
+    }
     __syncthreads();
     if (vec) {
       // thread t owns counters 8t .. 8t+7
@@ -1812,7 +1817,7 @@ __device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const ui
 #pragma unroll
       for (int i = 0; i < KPTA; ++i) {
         if ((uint32_t)(i * 32) + lane < wvalid) {
-          const uint32_t pos = cnt[(uint32_t)(k[i] >> gshift) & (nb - 1u)] + r[i];
+          const uint32_t pos = cnt[(uint32_t)(k[i] >> gshift) & (nb - 1u)] + (uint32_t)s_out[(uint32_t)i * NT + threadIdx.x];
           if (pos < len)
             s_keys[ssh + pos] = k[i];
           else
@@ -1849,7 +1854,7 @@ __device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const ui
 #pragma unroll
       for (int i = 0; i < KPTA; ++i) {
         if ((uint32_t)(i * 32) + lane < wvalid) {
-          const uint32_t pos = cnt[(uint32_t)(k[i] >> gshift) & (nb - 1u)] + r[i];
+          const uint32_t pos = cnt[(uint32_t)(k[i] >> gshift) & (nb - 1u)] + (uint32_t)s_out[(uint32_t)i * NT + threadIdx.x];
           if (pos < len)
             s_keys[pos] = k[i];
           else
