@@ -50,8 +50,15 @@ inline bool fmt_valid(int fmt) {
 // cap the CTA sort at 12 keys per lane (6144): buckets near 4096 keys are then
 // never joined into runs of ~8192 (which sort slower) and three CTAs fit an SM.
 // The u32 key-only scatter deals tiles of 512 x 24 keys at two CTAs per SM
-// (measured against 16, 20, 28 and 32 keys per thread: 24 is the fastest).
-template <class K, class V>
+// (measured against 16, 20, 28 and 32 keys per thread: 24 is the fastest at
+// 2^28 keys).  Geometry G = 1 serves calls of fewer than SMALL_TOTAL keys in
+// all: a wave of the large tiles (152 SMs x 2 CTAs x 12,288 keys) is about
+// 3.7M keys, and fewer tiles than CTA slots would leave SMs idle, so such u32
+// key-only calls take tiles of 512 x 16 keys at three CTAs per SM (measured:
+// 10^6 keys 0.201 -> 0.193 ms; a batch of 4096 arrays of 126K keys on average
+// is faster with the large tiles, 48.2 against 46.6 Gkeys/s).  The other key
+// types have one geometry (Cfg<K, V, 1> = Cfg<K, V, 0>).
+template <class K, class V, int G = 0>
 struct Cfg;
 template <>
 struct Cfg<uint32_t, NoVal> {
@@ -69,6 +76,26 @@ template <>
 struct Cfg<uint64_t, uint32_t> {
   static constexpr int SNT = 512, SKPT = 8, CNT = 512, CKPT = 8, WPB = 8, WKPT = 16;
 };
+template <class K, class V>
+struct Cfg<K, V, 1> : Cfg<K, V, 0> {};
+template <>
+struct Cfg<uint32_t, NoVal, 1> {
+  static constexpr int SNT = 512, SKPT = 16, CNT = 512, CKPT = 12, WPB = 8, WKPT = 16;
+};
+
+constexpr uint64_t SMALL_TOTAL = 1ull << 22;
+
+template <class K, class V>
+constexpr bool has_small_geometry() {
+  return std::is_same<K, uint32_t>::value && std::is_same<V, NoVal>::value;
+}
+
+// The geometry of a call of `narr` arrays holding `ntot` keys in all (the
+// workspace size follows the same rule, so it always matches the call).
+template <class K, class V>
+inline int geometry_of(uint64_t ntot, uint32_t narr) {
+  return (has_small_geometry<K, V>() && narr > 0u && ntot < SMALL_TOTAL) ? 1 : 0;
+}
 
 struct Layout {
   size_t ctl, arrs, root, segs0, segs1, hist0, hist1, cur0, cur1, owner, status, ctaq, wq, copyq, copyowner, total;
@@ -90,9 +117,9 @@ constexpr uint64_t lsd_min_n() {
   return (uint64_t)M * Cfg<K, V>::CNT * Cfg<K, V>::CKPT;
 }
 
-template <class K, class V>
+template <class K, class V, int G = 0>
 Layout make_layout(uint64_t ntot, uint32_t narr) {
-  using C = Cfg<K, V>;
+  using C = Cfg<K, V, G>;
   constexpr uint64_t TILE = (uint64_t)C::SNT * C::SKPT;
   constexpr uint64_t TCTA = (uint64_t)C::CNT * C::CKPT;
   Layout l{};
@@ -237,7 +264,8 @@ int check_arrays(const HostArr* arrs, uint32_t narr, uint64_t* ntot_out) {
 
 template <class K, class V>
 size_t workspace_bytes(uint64_t ntot, uint32_t narr) {
-  return make_layout<K, V>(ntot, narr).total;
+  return geometry_of<K, V>(ntot, narr) ? make_layout<K, V, 1>(ntot, narr).total
+                                       : make_layout<K, V, 0>(ntot, narr).total;
 }
 
 // Persistent grid sizes of every kernel of one key type on one device.
@@ -271,9 +299,9 @@ constexpr int key_type_of() {
                                        : (sizeof(K) == 8 ? DFR_U64_KV : DFR_U32_KV);
 }
 
-template <class K, class V>
+template <class K, class V, int G = 0>
 struct Kernels {
-  using C = Cfg<K, V>;
+  using C = Cfg<K, V, G>;
   static constexpr int SNT = C::SNT, SKPT = C::SKPT, TILE = SNT * SKPT;
   static constexpr int CNT = C::CNT, CKPT = C::CKPT, TCTA = CNT * CKPT;
   static constexpr int WPB = C::WPB, WKPT = C::WKPT, WCAP = 32 * WKPT;
@@ -300,8 +328,8 @@ struct Kernels {
   static constexpr auto lsd_fin = k_lsd_fin<K>;
 
   // grid_of(kernel, threads, dynamic smem) -> persistent grid (or < 0 on error)
-  template <class G>
-  static bool grids(G&& grid_of, Grids* g) {
+  template <class GridOf>
+  static bool grids(GridOf&& grid_of, Grids* g) {
     g->rc = grid_of((const void*)root_count, SNT, (size_t)0);
     g->rcl = grid_of((const void*)root_classify, 256, (size_t)0);
     g->lc = grid_of((const void*)level_count, SNT, (size_t)0);
@@ -336,10 +364,10 @@ inline uint32_t lsd_mode_of(const dfr_tune_t& t, const Layout& lay, uint32_t nar
 // root count (both digits) -> plan -> root classify -> pass 0 -> pass 1;
 // mode 2 = estimated pass 0 -> plan -> root count (skipped when the estimate
 // held) -> root classify -> pass 1.  The MSD levels follow either way.
-template <class K, class V, class Hook>
+template <class K, class V, int G, class Hook>
 void enqueue_sort(const Ctx& c, const Layout& lay, const Grids& g, uint32_t narr, uint32_t root_tiles,
                   unsigned long long ntot, const ArrDesc& a0, bool write_a0, cudaStream_t st, Hook&& hook) {
-  using T = Kernels<K, V>;
+  using T = Kernels<K, V, G>;
   const uint32_t mode = c.lsd_mode;
   const uint32_t root_words = (uint32_t)((size_t)narr * sizeof(RootAcc<K>) / 4);
   const uint32_t words = (uint32_t)(sizeof(Ctl) / 4) + root_words;
@@ -388,10 +416,10 @@ void enqueue_sort(const Ctx& c, const Layout& lay, const Grids& g, uint32_t narr
 // profiling hooks.  `batch` = the descriptor table is uploaded with one copy
 // (else the single descriptor rides in k_init's parameters, keeping the call
 // a pure kernel sequence).
-template <class K, class V>
-int run_sort(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws_bytes, cudaStream_t st,
-             int fmt = DFR_FMT_UNSIGNED) {
-  using T = Kernels<K, V>;
+template <class K, class V, int G>
+int run_sort_g(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws_bytes, cudaStream_t st,
+               int fmt) {
+  using T = Kernels<K, V, G>;
   if (!fmt_valid(fmt)) return DFR_ERR_INVALID_ARG;
   if (narr == 0) return DFR_OK;
   uint64_t ntot = 0;
@@ -400,7 +428,7 @@ int run_sort(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws
   bool any = false;
   for (uint32_t a = 0; a < narr; ++a) any = any || arrs[a].n > 1;
   if (!any) return DFR_OK;
-  const Layout lay = make_layout<K, V>(ntot, narr);
+  const Layout lay = make_layout<K, V, G>(ntot, narr);
   if (!ws || ((uintptr_t)ws & 255u)) return DFR_ERR_INVALID_ARG;
   if (ws_bytes < lay.total) return DFR_ERR_WORKSPACE;
   Ctx c = make_ctx(ws, lay, narr);
@@ -440,26 +468,36 @@ int run_sort(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws
   const uint32_t kf_grid = min_u32(rt, (uint32_t)g.kf);
   if (fmt != DFR_FMT_UNSIGNED)
     hook(PK_KEYFMT, st, [&] { T::keyfmt<<<kf_grid, T::SNT, 0, st>>>(c, tab[0], batch ? 0u : 1u, rt, (uint32_t)fmt, 1u); });
-  enqueue_sort<K, V>(c, lay, g, narr, rt, (unsigned long long)ntot, tab[0], !batch, st, hook);
+  enqueue_sort<K, V, G>(c, lay, g, narr, rt, (unsigned long long)ntot, tab[0], !batch, st, hook);
   if (fmt != DFR_FMT_UNSIGNED)
     hook(PK_KEYFMT, st, [&] { T::keyfmt<<<kf_grid, T::SNT, 0, st>>>(c, tab[0], batch ? 0u : 1u, rt, (uint32_t)fmt, 0u); });
   return cudaGetLastError() == cudaSuccess ? DFR_OK : DFR_ERR_CUDA;
 }
 
+// A call in the geometry its array sizes select (geometry_of).
+template <class K, class V>
+int run_sort(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws_bytes, cudaStream_t st,
+             int fmt = DFR_FMT_UNSIGNED) {
+  uint64_t ntot = 0;  // (each n is validated by run_sort_g)
+  for (uint32_t a = 0; a < narr; ++a) ntot += arrs[a].n;
+  return geometry_of<K, V>(ntot, narr) ? run_sort_g<K, V, 1>(arrs, narr, batch, ws, ws_bytes, st, fmt)
+                                       : run_sort_g<K, V, 0>(arrs, narr, batch, ws, ws_bytes, st, fmt);
+}
+
 // Capture one call's launch sequence into an executable CUDA graph bound to
 // these buffers and this workspace.  The descriptor table is uploaded now
 // (synchronously), so the captured sequence is kernels only.
-template <class K, class V>
-int build_graph(const HostArr* arrs, uint32_t narr, void* ws, size_t ws_bytes, cudaGraphExec_t* out,
-                uint32_t* nodes) {
-  using T = Kernels<K, V>;
+template <class K, class V, int G>
+int build_graph_g(const HostArr* arrs, uint32_t narr, void* ws, size_t ws_bytes, cudaGraphExec_t* out,
+                  uint32_t* nodes) {
+  using T = Kernels<K, V, G>;
   *out = nullptr;
   *nodes = 0;
   if (narr == 0) return DFR_ERR_INVALID_ARG;
   uint64_t ntot = 0;
   int rc = check_arrays<K, V>(arrs, narr, &ntot);
   if (rc != DFR_OK) return rc;
-  const Layout lay = make_layout<K, V>(ntot, narr);
+  const Layout lay = make_layout<K, V, G>(ntot, narr);
   if (!ws || ((uintptr_t)ws & 255u)) return DFR_ERR_INVALID_ARG;
   if (ws_bytes < lay.total) return DFR_ERR_WORKSPACE;
   Ctx c = make_ctx(ws, lay, narr);
@@ -489,7 +527,7 @@ int build_graph(const HostArr* arrs, uint32_t narr, void* ws, size_t ws_bytes, c
     rc = DFR_ERR_CUDA;
   } else {
     uint32_t n = 0;
-    enqueue_sort<K, V>(c, lay, g, narr, rt, (unsigned long long)ntot, tab[0], false, cs,
+    enqueue_sort<K, V, G>(c, lay, g, narr, rt, (unsigned long long)ntot, tab[0], false, cs,
                        [&n](int, cudaStream_t, auto&& fn) {
                          fn();
                          ++n;
@@ -502,6 +540,15 @@ int build_graph(const HostArr* arrs, uint32_t narr, void* ws, size_t ws_bytes, c
   cudaStreamDestroy(cs);
   if (rc != DFR_OK) *out = nullptr;
   return rc;
+}
+
+template <class K, class V>
+int build_graph(const HostArr* arrs, uint32_t narr, void* ws, size_t ws_bytes, cudaGraphExec_t* out,
+                uint32_t* nodes) {
+  uint64_t ntot = 0;  // (each n is validated by build_graph_g)
+  for (uint32_t a = 0; a < narr; ++a) ntot += arrs[a].n;
+  return geometry_of<K, V>(ntot, narr) ? build_graph_g<K, V, 1>(arrs, narr, ws, ws_bytes, out, nodes)
+                                       : build_graph_g<K, V, 0>(arrs, narr, ws, ws_bytes, out, nodes);
 }
 
 // Entry points instantiated per key type (dfr_u32.cu, ...).

@@ -54,12 +54,13 @@ std::mutex g_noalloc_mu;
 
 using K = uint32_t;
 using V = NoVal;
-using T = Kernels<K, V>;
+constexpr int G = 1;  // arrays of at most 2^20 keys: the small-array geometry
+using T = Kernels<K, V, G>;
 
 // Once per device, with the device current: resolve the scratch address and
 // the persistent grid sizes.  Returns a DFR status.
 int setup(int dev, NoAllocDevice* d) {
-  const size_t need = align256(kNoAllocMaxN * sizeof(K)) + make_layout<K, V>(kNoAllocMaxN, 1u).total;
+  const size_t need = align256(kNoAllocMaxN * sizeof(K)) + make_layout<K, V, G>(kNoAllocMaxN, 1u).total;
   if (need > kNoAllocScratchBytes) return DFR_ERR_WORKSPACE;
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return DFR_ERR_CUDA;
@@ -106,7 +107,7 @@ extern "C" int dfr_sort_u32_noalloc(uint32_t* keys, uint64_t n, dfr_stream_t str
   unsigned char* buf = d->base;
   void* ws = d->base + align256(n * sizeof(K));
   if (ranges_overlap(keys, n * sizeof(K), d->base, kNoAllocScratchBytes)) return DFR_ERR_INVALID_ARG;
-  const Layout lay = make_layout<K, V>(n, 1u);
+  const Layout lay = make_layout<K, V, G>(n, 1u);
   Ctx c = make_ctx(ws, lay, 1u);
   c.spin_limit = rt_spin_limit();
   c.force_timeout = 0u;
@@ -117,7 +118,7 @@ extern "C" int dfr_sort_u32_noalloc(uint32_t* keys, uint64_t n, dfr_stream_t str
   apply_tune(tune, d->sms, &g);
   const uint32_t rt = (uint32_t)((n + T::TILE - 1) / T::TILE);
   const ArrDesc a0{keys, buf, nullptr, nullptr, (uint32_t)n, 0u};
-  enqueue_sort<K, V>(c, lay, g, 1u, rt, (unsigned long long)n, a0, true, st,
+  enqueue_sort<K, V, G>(c, lay, g, 1u, rt, (unsigned long long)n, a0, true, st,
                      [](int, cudaStream_t, auto&& fn) {
                        fn();
                        rt_count_launch();
