@@ -45,8 +45,8 @@ import synth  # noqa: E402
 # key dealt), from profiles/k_scatter_u32_uniform_2^26.md; valid only for u32
 # key-only workloads while the kernel sources hash to SCATTER_SRC_SHA (else
 # the roofline's traffic is reported as null).
-SCATTER_NCU_BYTES_PER_KEY = 7.138
-SCATTER_SRC_SHA = "aa1e943d1ba8b073"
+SCATTER_NCU_BYTES_PER_KEY = 7.140
+SCATTER_SRC_SHA = "07c963dfd0f1f19e"
 
 WORKLOADS = {
     "plain_u32_2^28": dict(kind="plain", key="u32", n=1 << 28, dists=list(synth.U32_DISTRIBUTIONS)),

@@ -262,10 +262,16 @@ int check_arrays(const HostArr* arrs, uint32_t narr, uint64_t* ntot_out) {
   return DFR_OK;
 }
 
+// The workspace a call of ntot keys in narr arrays needs: the larger of the
+// two geometries' layouts, so that the size never decreases with ntot (a
+// workspace sized for n keys serves every call of fewer keys, whichever
+// geometry that call selects).
 template <class K, class V>
 size_t workspace_bytes(uint64_t ntot, uint32_t narr) {
-  return geometry_of<K, V>(ntot, narr) ? make_layout<K, V, 1>(ntot, narr).total
-                                       : make_layout<K, V, 0>(ntot, narr).total;
+  if constexpr (has_small_geometry<K, V>())
+    return std::max(make_layout<K, V, 0>(ntot, narr).total, make_layout<K, V, 1>(ntot, narr).total);
+  else
+    return make_layout<K, V, 0>(ntot, narr).total;
 }
 
 // Persistent grid sizes of every kernel of one key type on one device.

@@ -180,3 +180,20 @@ def test_key_format_host_checks(lib):
     assert dfr.dfr_sort_format(dfr.DFR_U64, dfr.DFR_FMT_SIGNED, 0x1000, 0, 0x2000, 0, 1, 0, 0, stream=0) == dfr.DFR_OK
     names = [lib.dfr_profile_kind_name(i) for i in range(dfr.DFR_PROFILE_KINDS)]
     assert names[-3:] == [b"keyfmt", b"lsd_pass", b"lsd_plan"]
+
+
+def test_workspace_bytes_never_decrease(lib):
+    """A workspace sized for n keys must serve every call of fewer keys, also
+    across the sizes where the plan switches the scatter geometry (2^22 keys
+    in all) or starts to allow the LSD phase (dfr_lsd_min_keys)."""
+    for kt in (dfr.DFR_U32, dfr.DFR_U64, dfr.DFR_U64_KV, dfr.DFR_U32_KV):
+        edges = [1 << 22, dfr.dfr_lsd_min_keys(kt)]
+        pts = set([1, 2, 3, 31, 33, 4096, 6145, 8193, 12289, 1 << 20, 1 << 24, 1 << 28, dfr.DFR_MAX_N])
+        for e in edges:
+            pts.update(range(e - 20000, e + 20000, 331))
+            pts.update((e - 1, e, e + 1))
+        prev = 0
+        for n in sorted(pts):
+            w = dfr.dfr_workspace_bytes(kt, n)
+            assert w >= prev, (kt, n, w, prev)
+            prev = w

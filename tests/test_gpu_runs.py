@@ -126,3 +126,20 @@ def test_dominant_digit(dfr, share):
     b = a.copy()
     b[heavy] = np.uint32(0x5A3C1234)
     _check(dfr, b)
+
+
+def test_workspace_sized_above_the_geometry_switch(dfr):
+    # a workspace sized for more than 2^22 keys (large-tile geometry) serves a
+    # call just below 2^22 keys (small-tile geometry)
+    import torch
+
+    n_cap = (1 << 22) + 5
+    s = dfr.Sorter(dfr.DFR_U32, n_cap)
+    for n in ((1 << 22) - 3, (1 << 22) - 100_000, 1 << 22, n_cap):
+        a = synth.uniform_u32(n, synth.BASE_SEED + 2800 + n)
+        dk = dfr.to_device(a)
+        assert s.sort_(dk) == dfr.DFR_OK
+        assert s.device_status() == dfr.DFR_OK
+        assert np.array_equal(dfr.to_numpy(dk, np.uint32), oracle.sort_u32(a)), n
+    del s
+    torch.cuda.empty_cache()
