@@ -248,3 +248,57 @@ def test_forced_timeout_in_lsd_pass(dfr):
         k, _, st, stats = run(dfr, a)
     assert st == dfr.DFR_OK and stats["schedule"] == dfr.DFR_SCHED_LSD
     assert np.array_equal(k, oracle.sort_u32(a))
+
+
+@pytest.mark.parametrize("sched", [1, 2])
+def test_lsd_with_key_formats(dfr, sched):
+    # signed and IEEE-float keys are mapped to their unsigned images in
+    # place, sorted (here through the LSD phase) and mapped back
+    import torch
+
+    n = dfr.dfr_lsd_min_keys(dfr.DFR_U32) + 1001
+    g = np.random.default_rng(3100 + sched)
+    a = g.integers(-(1 << 31), (1 << 31) - 1, size=n, dtype=np.int64).astype(np.int32)
+    f = (g.standard_normal(n) * 1e6).astype(np.float64)
+    v = synth.index_payload(f.size)
+    with forced_schedule(dfr, sched):
+        s = sorter(dfr, dfr.DFR_U32, n)
+        dk = dfr.to_device(a)
+        assert s.sort_(dk, key_format=dfr.DFR_FMT_SIGNED) == dfr.DFR_OK
+        assert s.device_status() == dfr.DFR_OK
+        st = s.stats()
+        assert np.array_equal(dk.cpu().numpy(), oracle.sort_format(0, dfr.DFR_FMT_SIGNED, a))
+        assert st["schedule"] == sched
+        s2 = sorter(dfr, dfr.DFR_U64_KV, f.size)
+        dk2 = dfr.to_device(f)
+        dv2 = dfr.to_device(v)
+        assert s2.sort_(dk2, dv2, key_format=dfr.DFR_FMT_FLOAT | dfr.DFR_FMT_DESCENDING) == dfr.DFR_OK
+        assert s2.device_status() == dfr.DFR_OK
+        ek, ev = oracle.sort_format(2, dfr.DFR_FMT_FLOAT | dfr.DFR_FMT_DESCENDING, f, v)
+        assert np.array_equal(dk2.cpu().numpy().view(np.float64), ek)
+        assert np.array_equal(dfr.to_numpy(dv2, np.uint32), ev)
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("sched", [1, 2])
+def test_lsd_through_the_batch_entry(dfr, sched):
+    # a batch of one array takes the LSD phase too; its descriptor reaches
+    # the device by a copy instead of the first kernel's parameters
+    import torch
+
+    n = dfr.dfr_lsd_min_keys(dfr.DFR_U64_KV) + 12_345
+    a = synth.uniform64_u64(n, synth.BASE_SEED + 3200 + sched)
+    v = synth.index_payload(n)
+    keys, vals = dfr.to_device(a), dfr.to_device(v)
+    kbuf, vbuf = torch.empty_like(keys), torch.empty_like(vals)
+    seg = (dfr.DFR_U64_KV, keys, vals, kbuf, vbuf, n)
+    wsb = dfr.dfr_batch_workspace_bytes([seg])
+    ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
+    with forced_schedule(dfr, sched):
+        assert dfr.dfr_sort_batch([seg], ws, wsb) == dfr.DFR_OK
+        torch.cuda.synchronize()
+        assert dfr.dfr_last_device_status(ws) == dfr.DFR_OK
+        assert dfr.dfr_get_stats(ws)["schedule"] == sched
+    ok, ov = oracle.sort_u64_kv(a, v)
+    assert np.array_equal(dfr.to_numpy(keys, np.uint64), ok)
+    assert np.array_equal(dfr.to_numpy(vals, np.uint32), ov)
