@@ -312,12 +312,19 @@ int dfr_server_set_limits(dfr_server_t* server, uint32_t max_batch, uint32_t max
 /* dfr_poll -- *done = 1 once the request's sort has completed on the device;
  * then *latency_us (may be NULL) = completion time - submission time in
  * microseconds, the ticket is released and the request's status is returned
- * (DFR_OK, or a device error: DFR_ERR_TIMEOUT, DFR_ERR_BOUNDS,
- * DFR_ERR_WORKSPACE).  While pending: *done = 0 and DFR_OK.  An unknown or
- * released ticket gives DFR_ERR_INVALID_ARG. */
+ * (DFR_OK; a device error: DFR_ERR_TIMEOUT, DFR_ERR_BOUNDS,
+ * DFR_ERR_WORKSPACE; or DFR_ERR_CUDA when its batch could not be enqueued).
+ * While pending: *done = 0 and DFR_OK.  An unknown or released ticket gives
+ * DFR_ERR_INVALID_ARG.
+ *
+ * A ticket has one consumer: the server's calls may come from any threads,
+ * but one ticket is polled or waited on by one thread at a time (a second
+ * thread's dfr_wait on a ticket that another thread's call releases reads a
+ * freed request). */
 int dfr_poll(dfr_server_t* server, uint64_t ticket, int* done, double* latency_us);
 
-/* dfr_wait -- block until the request is done; then as dfr_poll. */
+/* dfr_wait -- block until the request is done; then as dfr_poll (one
+ * consumer per ticket, as there). */
 int dfr_wait(dfr_server_t* server, uint64_t ticket, double* latency_us);
 
 /* dfr_server_stats -- batches launched so far, requests pending and batches

@@ -410,7 +410,10 @@ class Sorter:
 
         self.key_type = key_type
         self.capacity = int(capacity)
-        self.device = torch.device(device)
+        dev = torch.device(device)
+        if dev.type == "cuda" and dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
         kb = KEY_BYTES[key_type]
         kdt = torch.int32 if kb == 4 else torch.int64
         self.kbuf = torch.empty(max(1, self.capacity), dtype=kdt, device=self.device)
@@ -420,11 +423,35 @@ class Sorter:
         # zeroed once so the status word reads DFR_OK before the first call
         self.ws = torch.zeros(self.ws_bytes, dtype=torch.uint8, device=self.device)
 
+    def _arg(self, t, name: str, n: int, item_bytes: int) -> None:
+        """The C entry points take a bare pointer and trust it to hold `n`
+        contiguous items: check that tensor `t` does, on this sorter's device."""
+        if t is None:
+            if n:
+                raise ValueError("%s is required to sort %d keys" % (name, n))
+            return
+        if t.element_size() != item_bytes:
+            raise ValueError("%s has %d-byte items; this key type needs %d" % (name, t.element_size(), item_bytes))
+        if t.numel() < n:
+            raise ValueError("%s holds %d items, fewer than n = %d" % (name, t.numel(), n))
+        if not t.is_contiguous():
+            raise ValueError("%s is not contiguous" % name)
+        if t.device != self.device:
+            raise ValueError("%s is on %s; this sorter's buffers are on %s" % (name, t.device, self.device))
+
     def sort_(self, keys, vals=None, n=None, stream=None, key_format=DFR_FMT_UNSIGNED) -> int:
+        """Sort the first `n` (default: all) keys of `keys` in place, with their
+        payloads `vals` for the kv key types; raises ValueError for a tensor
+        that cannot hold them and DfrError for a status other than DFR_OK."""
         n = int(keys.numel() if n is None else n)
-        if n > self.capacity:
-            raise ValueError("array of %d keys exceeds capacity %d" % (n, self.capacity))
+        if n < 0 or n > self.capacity:
+            raise ValueError("array of %d keys outside this sorter's capacity %d" % (n, self.capacity))
         kt = self.key_type
+        self._arg(keys, "keys", n, KEY_BYTES[kt])
+        if HAS_VALS[kt]:
+            self._arg(vals, "vals", n, 4)
+        elif vals is not None:
+            raise ValueError("payloads given to a key-only sorter")
         if key_format != DFR_FMT_UNSIGNED:
             rc = dfr_sort_format(kt, key_format, keys, vals, self.kbuf, self.vbuf, n, self.ws, self.ws_bytes, stream)
         elif kt == DFR_U32:
