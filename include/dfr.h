@@ -24,7 +24,10 @@
  *   - n == 0 and n == 1 return DFR_OK without touching the GPU.
  *   - A single array may hold at most DFR_MAX_N keys.
  *   - Ranges [keys, keys+n) and [buf, buf+n) (and the payload pair) must not
- *     overlap; overlap returns DFR_ERR_INVALID_ARG.
+ *     overlap; overlap returns DFR_ERR_INVALID_ARG.  The workspace must not
+ *     overlap any of them either, and the arrays of one batch must be
+ *     disjoint from one another; these two are not checked (the result is
+ *     undefined).
  *   - The workspace must be at least dfr_workspace_bytes() bytes and 256-byte
  *     aligned.  One workspace serves one call at a time: calls sharing a
  *     workspace must be ordered on one stream (or otherwise serialised).
@@ -201,8 +204,9 @@ int dfr_batch_workspace_bytes(const dfr_segment_t* segs, uint32_t count, size_t*
  * launches as one.  Each array's result is exactly that of sorting it alone.
  * The descriptor table is copied to the device before the call returns, so
  * `segs` may be reused at once.
- * Errors: DFR_ERR_INVALID_ARG for mixed key types, null pointers, overlap or
- * an array above DFR_MAX_N; DFR_ERR_WORKSPACE for a short workspace.
+ * Errors: DFR_ERR_INVALID_ARG for mixed key types, null pointers, overlap
+ * within one array's buffers or an array above DFR_MAX_N; DFR_ERR_WORKSPACE
+ * for a short workspace.  Distinct arrays must not share memory (unchecked).
  */
 int dfr_sort_batch(const dfr_segment_t* segs, uint32_t count, void* ws, size_t ws_bytes,
                    dfr_stream_t stream);
