@@ -688,6 +688,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample", type=int, default=1 << 26)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-streams", type=int, default=3, help="streams (device buffer sets) of the end-to-end leg")
     ap.add_argument("--dists", default="", help="comma-separated subset of the workload's distributions")
     ap.add_argument("--requests", type=int, default=0, help="served workload: requests per pass")
     ap.add_argument("--serve-streams", type=int, default=4, help="served workload: server streams")
@@ -878,30 +879,34 @@ def main():
     kernel_share = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}
 
     # End to end through the C ABI: pinned host keys -> device -> sort -> host.
-    # Two streams with a device buffer set each: the upload of the step's next
-    # array overlaps the sort and the download of the previous one (the two
+    # Arrays go round-robin to `ns` streams, each with its own device buffer
+    # set; a stream's next upload waits for its previous download, so with
+    # three or more streams the upload engine never waits on a sort and the
+    # uploads, sorts and downloads of consecutive arrays all overlap (the two
     # copy directions run on separate copy engines).  Every host<->device copy
     # of the step is inside the timed region.
     e2e = None
     if not args.no_e2e:
+        ns = max(1, args.e2e_streams)
         host_in = {d: torch.from_numpy(a.view(np.int32) if a.dtype == np.uint32 else a.view(np.int64)).pin_memory()
                    for d, a in inputs.items()}
-        host_out = [torch.empty_like(next(iter(host_in.values()))).pin_memory() for _ in range(2)]
+        host_out = [torch.empty_like(next(iter(host_in.values()))).pin_memory() for _ in range(ns)]
         hv_in = torch.from_numpy(synth.index_payload(n).view(np.int32)).pin_memory() if kv else None
-        hv_out = [torch.empty_like(hv_in).pin_memory() for _ in range(2)] if kv else [None, None]
-        streams = [stream, torch.cuda.Stream(dev)]
-        works = [work, torch.empty_like(work)]
-        valss = [vals, torch.empty_like(vals)] if kv else [None, None]
-        sorters = [sorter, dfr.Sorter(kt, n, dev)]
+        hv_out = [torch.empty_like(hv_in).pin_memory() for _ in range(ns)] if kv else [None] * ns
+        streams = [stream] + [torch.cuda.Stream(dev) for _ in range(ns - 1)]
+        works = [work] + [torch.empty_like(work) for _ in range(ns - 1)]
+        valss = [vals] + [torch.empty_like(vals) for _ in range(ns - 1)] if kv else [None] * ns
+        sorters = [sorter] + [dfr.Sorter(kt, n, dev) for _ in range(ns - 1)]
         e2e_ms = []
         for step in range(max(1, min(args.steps, 3))):
             flush.fill_(1)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(streams[0])
-            streams[1].wait_event(e0)
+            for s in streams[1:]:
+                s.wait_event(e0)
             for i, d in enumerate(inputs):
-                j = i % 2
+                j = i % ns
                 with torch.cuda.stream(streams[j]):
                     works[j].copy_(host_in[d], non_blocking=True)
                     if kv:
@@ -910,21 +915,23 @@ def main():
                     host_out[j].copy_(works[j], non_blocking=True)
                     if kv:
                         hv_out[j].copy_(valss[j], non_blocking=True)
-            joined = torch.cuda.Event()
-            joined.record(streams[1])
-            streams[0].wait_event(joined)
+            for s in streams[1:]:
+                joined = torch.cuda.Event()
+                joined.record(s)
+                streams[0].wait_event(joined)
             e1.record(streams[0])
             e1.synchronize()
             e2e_ms.append(e0.elapsed_time(e1))
-        for j in range(2):
+        for j in range(ns):
             st = sorters[j].device_status(streams[j])
             if st != dfr.DFR_OK:
                 raise RuntimeError("device status %s in the end-to-end run" % dfr.dfr_status_string(st))
         ms, e2e_rate = job_rate(sum(e2e_ms) / len(e2e_ms), keys_per_step, world, dev)
         e2e = {"value": e2e_rate, "unit": "Gkeys/s",
                "h2d_bytes_per_step": keys_per_step * rec, "d2h_bytes_per_step": keys_per_step * rec,
-               "ms_per_step": ms, "streams": 2,
-               "overlap": "the next array's upload overlaps the previous array's sort and download"}
+               "ms_per_step": ms, "streams": ns,
+               "overlap": "arrays round-robin over %d streams: uploads, sorts and downloads of consecutive arrays "
+                          "overlap" % ns}
 
     cpu = None
     if rank == 0 and world == 1:
