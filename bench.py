@@ -100,56 +100,145 @@ def gen_inputs(wl: dict, seed_off: int):
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """nvidia-smi clock and throttle-reason sampling over the timed region.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    nvidia-smi polls every `interval_ms` (20 ms, so that a timed region of a
+    few hundred milliseconds holds several samples; 200 ms if the short
+    interval yields no sample within a few seconds; that fallback asks for
+    the fields without the stamp) and stamps each sample.
+    start() returns once the first sample has been written, so sampling is
+    live before the warm-up; mark_start() / mark_end() bracket the timed
+    region; stop() summarises the samples stamped inside it, widened by one
+    interval on each side (all samples, if none falls inside or the stamps
+    cannot be read).  Nothing here raises: without nvidia-smi the summary is
+    None."""
 
-    def __init__(self, index: int):
+    Q_PLAIN = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    Q = "timestamp," + Q_PLAIN
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    FALLBACK_MS = 200
+    FIRST_SAMPLE_S = 5.0
+
+    def __init__(self, index: int, interval_ms: int = 20, exe: str = "nvidia-smi"):
         self.index = index
+        self.interval_ms = interval_ms
+        self.exe = exe
         self.proc = None
+        self.f = None
+        self.t0 = self.t1 = None
         self.path = os.path.join("/tmp", "dfr_clocks_%d_%d.csv" % (os.getpid(), index))
 
-    def start(self):
+    def _launch(self, interval_ms: int, query: str) -> None:
+        self.f = open(self.path, "w")
+        self.interval_ms = interval_ms
+        self.proc = subprocess.Popen([self.exe, "-i", str(self.index), "--query-gpu=" + query,
+                                      "--format=csv,noheader,nounits", "-lms", str(interval_ms)],
+                                     stdout=self.f, stderr=subprocess.DEVNULL)
+
+    def _has_sample(self) -> bool:
+        with open(self.path) as f:
+            return self.summarise(f.read().splitlines(), None, None, self.interval_ms) is not None
+
+    def _wait_first_sample(self) -> bool:
+        """True once a readable sample line is in the file (an error message
+        printed instead of samples does not count)."""
+        end = time.monotonic() + self.FIRST_SAMPLE_S
+        while time.monotonic() < end:
+            if self._has_sample():
+                return True
+            if self.proc.poll() is not None:  # exited, e.g. refused the interval or a field
+                return self._has_sample()
+            time.sleep(0.01)
+        return False
+
+    def _halt(self) -> None:
+        if self.proc is not None:
+            try:
+                self.proc.terminate()
+                self.proc.wait(timeout=5)
+            except Exception:
+                try:
+                    self.proc.kill()
+                    self.proc.wait(timeout=5)
+                except Exception:
+                    pass
+        if self.f is not None:
+            self.f.close()
+
+    def start(self) -> None:
         try:
-            self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            self._launch(self.interval_ms, self.Q)
+            if not self._wait_first_sample():
+                self._halt()
+                self._launch(self.FALLBACK_MS, self.Q_PLAIN)
+                self._wait_first_sample()
         except Exception:
+            self._halt()
             self.proc = None
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+
+    def mark_start(self) -> None:
+        self.t0 = time.time()
+
+    def mark_end(self) -> None:
+        self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
             return None
-        self.proc.terminate()
         try:
-            self.proc.wait(timeout=5)
+            self._halt()
+            with open(self.path) as f:
+                lines = f.read().splitlines()
+            os.unlink(self.path)
+            return self.summarise(lines, self.t0, self.t1, self.interval_ms)
         except Exception:
-            self.proc.kill()
-        self.f.close()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        with open(self.path) as f:
-            for line in f:
-                p = [x.strip() for x in line.split(",")]
-                if len(p) < 9:
-                    continue
-                try:
-                    sm.append(float(p[1]))
-                    mx.append(float(p[2]))
-                except ValueError:
-                    continue
-                for nm, v in zip(names, p[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(nm)
-        os.unlink(self.path)
-        if not sm:
             return None
+
+    @classmethod
+    def summarise(cls, lines, t0, t1, interval_ms):
+        """Median loaded SM clock, max clock and the throttle reasons seen,
+        over the samples of [t0, t1] widened by one interval (all samples
+        when the window is unknown or holds none)."""
+        import datetime
+
+        rows = []
+        for line in lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) == 9:  # the fallback query: no stamp
+                p = [""] + p
+            if len(p) < 10:
+                continue
+            try:
+                sm, mx = float(p[2]), float(p[3])
+            except ValueError:
+                continue
+            try:
+                t = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                t = None
+            reasons = {nm for nm, v in zip(cls.REASONS, p[6:10]) if v.lower().startswith("active")}
+            rows.append((t, sm, mx, reasons))
+        if not rows:
+            return None
+        window = "run"
+        use = rows
+        if t0 is not None and t1 is not None:
+            pad = interval_ms * 1e-3
+            inside = [r for r in rows if r[0] is not None and t0 - pad <= r[0] <= t1 + pad]
+            if inside:
+                use, window = inside, "timed"
+        sm = [r[1] for r in use]
         loaded = [x for x in sm if x > 0.5 * max(sm)] or sm
-        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = set().union(*(r[3] for r in use))
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": sorted(reasons), "samples": len(use), "samples_total": len(rows),
+                "interval_ms": interval_ms, "window": window}
 
 
 def dist_setup():
@@ -359,10 +448,12 @@ def run_batch(args, wl, dfr, dev, world, rank):
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
+    clocks.mark_start()
     l0 = dfr.dfr_launch_count()
     t_batch = timed(batched, args.steps)
     launches = dfr.dfr_launch_count() - l0
     torch.cuda.synchronize()
+    clocks.mark_end()
     barrier(world)
     clk = clocks.stop()
     t_plain = timed(plain, max(1, min(args.steps, 3)))
@@ -585,6 +676,7 @@ def run_served(args, wl, dfr, dev, world, rank):
 
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
+    clocks.mark_start()
     l0 = dfr.dfr_launch_count()
     closed = one(True, None)
     peak_keys_s = closed["gkeys_s"] * 1e9
@@ -595,6 +687,7 @@ def run_served(args, wl, dfr, dev, world, rank):
                                           "batched": one(True, rate),
                                           "fifo_plain": one(False, rate)}
     launches = dfr.dfr_launch_count() - l0
+    clocks.mark_end()
     clk = clocks.stop()
     closed_plain = one(False, None, min(R, 20_000))
 
@@ -755,8 +848,8 @@ def main():
         sorter.sort_(work, vals, n, stream)
         ev1.record(stream)
 
-    # warm-up (the clock sampler runs from here through the timed steps: the
-    # timed region alone is shorter than a few sampling periods)
+    # warm-up (the clock sampler is live from here; its summary keeps the
+    # samples stamped within the timed steps)
     clocks = ClockSampler(local)
     clocks.start()
     for _ in range(args.warmup):
@@ -771,6 +864,7 @@ def main():
 
     barrier(world)
     torch.cuda.synchronize()
+    clocks.mark_start()
     launches0 = dfr.dfr_launch_count()
     evs = []
     for _ in range(args.steps):
@@ -781,6 +875,7 @@ def main():
             row.append((d, e0, e1))
         evs.append(row)
     torch.cuda.synchronize()
+    clocks.mark_end()
     launches = dfr.dfr_launch_count() - launches0
     barrier(world)
     clk = clocks.stop()
