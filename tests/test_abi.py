@@ -197,3 +197,22 @@ def test_workspace_bytes_never_decrease(lib):
             w = dfr.dfr_workspace_bytes(kt, n)
             assert w >= prev, (kt, n, w, prev)
             prev = w
+
+
+def test_checked_in_tune_table_is_the_compiled_one(lib):
+    """The tuner's JSON record and the table compiled into the library (from
+    csrc/dfr_tune_table.inc) hold the same plan for every key type and size
+    class."""
+    import json
+
+    from paper_2207_14334_gb300 import tune
+
+    with open(os.path.join(os.path.dirname(tune.INC), "..", "tune_table.json")) as f:
+        table = json.load(f)["table"]
+    assert dfr.dfr_tune_reset() == dfr.DFR_OK
+    for name in tune.KEY_TYPES:
+        kt = getattr(dfr, name)
+        for c in range(dfr.DFR_TUNE_CLASSES):
+            rec = table[name][str(c)]
+            want = {f: int(rec.get(f, 0)) for f in tune.FIELDS}
+            assert dfr.dfr_tune_get(kt, c) == want, (name, c)
