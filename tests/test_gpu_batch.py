@@ -78,3 +78,63 @@ def test_batch_u64_kv(dfr):
     for k, v, gk, gv in zip(keys, vals, ok, ov):
         ek, ev = oracle.sort_u64_kv(k, v)
         assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
+
+
+def _segmented(dfr, key_type, a, v, lens, gaps):
+    """dfr_sort_batch over slices of one array (a segmented sort): slice i
+    holds lens[i] keys and starts gaps[i] keys after the previous slice ends;
+    the keys in the gaps are not part of any segment and must not move."""
+    import torch
+
+    kb = dfr.KEY_BYTES[key_type]
+    dk = dfr.to_device(a)
+    dv = dfr.to_device(v) if v is not None else None
+    kscratch = torch.empty_like(dk)
+    vscratch = torch.empty_like(dv) if dv is not None else None
+    segs, spans, o = [], [], 0
+    for n, gap in zip(lens, gaps):
+        o += gap
+        if n:
+            segs.append((key_type, dk.data_ptr() + kb * o, dv.data_ptr() + 4 * o if dv is not None else 0,
+                         kscratch.data_ptr() + kb * o, vscratch.data_ptr() + 4 * o if dv is not None else 0, n))
+        else:
+            segs.append((key_type, 0, 0, 0, 0, 0))
+        spans.append((o, n))
+        o += n
+    assert o <= a.size
+    ws_bytes = dfr.dfr_batch_workspace_bytes(segs)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dk.device)
+    assert dfr.dfr_sort_batch(segs, ws, ws_bytes) == dfr.DFR_OK
+    assert dfr.dfr_last_device_status(ws) == dfr.DFR_OK
+    got_k = dfr.to_numpy(dk, a.dtype)
+    got_v = dfr.to_numpy(dv, np.uint32) if dv is not None else None
+    return got_k, got_v, spans
+
+
+def _segment_plan(seed, count, hi, extra):
+    g = np.random.default_rng(seed)
+    lens = [int(x) for x in g.integers(0, hi, size=count)] + list(extra)
+    g.shuffle(lens)
+    gaps = [int(x) for x in g.integers(0, 5, size=len(lens))]
+    return lens, gaps, sum(lens) + sum(gaps) + 3
+
+
+def test_batch_as_segmented_sort_u32(dfr):
+    lens, gaps, total = _segment_plan(5100, 300, 40_000, [0, 1, 2, 33, 4097, 200_003])
+    a = synth.uniform_u32(total, synth.BASE_SEED + 5100)
+    got, _, spans = _segmented(dfr, dfr.DFR_U32, a, None, lens, gaps)
+    want = a.copy()
+    for o, n in spans:
+        want[o:o + n] = oracle.sort_u32(a[o:o + n])
+    assert np.array_equal(got, want)
+
+
+def test_batch_as_segmented_sort_u64_kv(dfr):
+    lens, gaps, total = _segment_plan(5200, 60, 30_000, [0, 1, 3, 70_001])
+    a = synth.dup90_u64(total, synth.BASE_SEED + 5200)
+    v = synth.index_payload(total)
+    got_k, got_v, spans = _segmented(dfr, dfr.DFR_U64_KV, a, v, lens, gaps)
+    want_k, want_v = a.copy(), v.copy()
+    for o, n in spans:
+        want_k[o:o + n], want_v[o:o + n] = oracle.sort_u64_kv(a[o:o + n], v[o:o + n])
+    assert np.array_equal(got_k, want_k) and np.array_equal(got_v, want_v)
