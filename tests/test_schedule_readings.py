@@ -107,3 +107,33 @@ def test_estimated_deal_reads_in_stable_order(shift):
         order, nover = estimated_deal(keys, shift, cap)
         assert order == oracle.counting_pass_u32(keys, shift).tolist()
         assert nover == oracle.overflow_count(keys, shift, cap)
+
+
+def test_runs_of_small_buckets_sort_as_each_bucket_alone():
+    """Section "Diverting Fast Radix" sorts the small buckets in bulk: after a
+    stable deal on the top digit, consecutive small buckets are joined into
+    runs and each run is sorted stably as one piece.  Because the buckets of a
+    run are adjacent, ordered and never share a key, that equals sorting each
+    bucket alone and equals the plain stable sort, payloads included."""
+    g = np.random.default_rng(500)
+    for trial in range(6):
+        n = int(g.integers(1, 3000))
+        keys = g.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
+        if trial % 2:
+            keys = g.choice(keys[: max(1, n // 30)], size=n)  # heavy ties inside buckets
+        vals = np.arange(n, dtype=np.uint32)
+        recs = counting_deal(list(zip((int(k) for k in keys), (int(v) for v in vals))), 24)
+        bounds = [0]
+        for i in range(1, n):
+            if (recs[i][0] >> 24) != (recs[i - 1][0] >> 24):
+                bounds.append(i)
+        bounds.append(n)
+        # join consecutive buckets into runs of random lengths, then sort each run
+        out, b = [], 0
+        while b < len(bounds) - 1:
+            e = min(len(bounds) - 1, b + int(g.integers(1, 6)))
+            out.extend(stable_insertion_sort(recs[bounds[b]:bounds[e]]))
+            b = e
+        ok, ov = oracle.sort_u32_kv(keys, vals)
+        assert [r[0] for r in out] == ok.tolist()
+        assert [r[1] for r in out] == ov.tolist()
