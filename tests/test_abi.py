@@ -216,3 +216,20 @@ def test_checked_in_tune_table_is_the_compiled_one(lib):
             rec = table[name][str(c)]
             want = {f: int(rec.get(f, 0)) for f in tune.FIELDS}
             assert dfr.dfr_tune_get(kt, c) == want, (name, c)
+
+
+def test_lsd_minimum_and_size_classes(lib):
+    """The LSD schedules apply from 256 x the CTA sort's capacity (6144 u32
+    keys; 4096 u64 keys or key-value records): below that the top digit's
+    buckets already fit one CTA sort on average, and dealing a second top
+    digit first would not pay.  Size class c covers mean array lengths
+    [2^(10+2c), 2^(12+2c)); class 0 everything below 2^12, the last class
+    2^28 and up."""
+    assert dfr.dfr_lsd_min_keys(dfr.DFR_U32) == 256 * 6144
+    for kt in (dfr.DFR_U64, dfr.DFR_U64_KV, dfr.DFR_U32_KV):
+        assert dfr.dfr_lsd_min_keys(kt) == 256 * 4096
+    for c in range(1, dfr.DFR_TUNE_CLASSES - 1):
+        lo, hi = 1 << (10 + 2 * c), 1 << (12 + 2 * c)
+        assert dfr.dfr_tune_class(lo) == c and dfr.dfr_tune_class(hi - 1) == c and dfr.dfr_tune_class(hi) == c + 1
+    assert dfr.dfr_tune_class((1 << 12) - 1) == 0
+    assert dfr.dfr_tune_class(1 << 40) == dfr.DFR_TUNE_CLASSES - 1
