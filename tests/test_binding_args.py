@@ -54,3 +54,16 @@ def test_other_device(lib):
     # a tensor on another device than the sorter's buffers
     s = dfr.Sorter(dfr.DFR_U32, 64, device="cpu")
     refused(s, torch.empty(64, dtype=torch.int32, device="meta"))
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    # with the CUDA library absent every call raises; nothing falls back to a
+    # CPU path
+    monkeypatch.setattr(dfr, "LIB_PATH", str(tmp_path / "libdfr.so"))
+    monkeypatch.setattr(dfr, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        dfr.load()
+    with pytest.raises(RuntimeError):
+        dfr.dfr_workspace_bytes(dfr.DFR_U32, 1000)
+    with pytest.raises(RuntimeError):
+        dfr.dfr_sort_u32(0, 0, 10, 0, 0, stream=0)
