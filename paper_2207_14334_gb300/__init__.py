@@ -8,10 +8,18 @@ current torch stream).  PyTorch is only used for device memory and streams.
 
 There is no fallback: if libdfr.so has not been built, importing works but
 the first call raises, naming the build step.
+
+Two environment variables configure the library when it is first loaded
+(through the C entry points, as a caller could): DFR_TUNE_FILE names a
+launch-plan table in the autotuner's JSON format, whose entries override the
+built-in ones (dfr_tune_set); DFR_SPIN_LIMIT sets how many iterations a
+device-side wait may spin before it reports DFR_ERR_TIMEOUT (dfr_set_debug).
+A file or value the library refuses makes the load raise.
 """
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 import threading
 
@@ -55,9 +63,9 @@ HAS_VALS = {DFR_U32: False, DFR_U64: False, DFR_U64_KV: True, DFR_U32_KV: True}
 
 
 class DfrError(RuntimeError):
-    def __init__(self, code: int, what: str = ""):
+    def __init__(self, code: int, what: str = "", text: str | None = None):
         self.code = code
-        super().__init__("%s: %s (code %d)" % (what or "dfr", _status_text(code), code))
+        super().__init__("%s: %s (code %d)" % (what or "dfr", _status_text(code) if text is None else text, code))
 
 
 _u64 = ctypes.c_uint64
@@ -149,8 +157,44 @@ def load() -> ctypes.CDLL:
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
+            _apply_env_config(lib)
             _lib = lib
     return _lib
+
+
+_KEY_TYPE_NAMES = {"DFR_U32": DFR_U32, "DFR_U64": DFR_U64, "DFR_U64_KV": DFR_U64_KV, "DFR_U32_KV": DFR_U32_KV}
+
+
+def _apply_env_config(lib) -> None:
+    """Apply DFR_TUNE_FILE and DFR_SPIN_LIMIT (see the module docstring); with
+    neither set, nothing is called."""
+    path = os.environ.get("DFR_TUNE_FILE")
+    if path:
+        with open(path) as f:
+            doc = json.load(f)
+        table = doc.get("table", doc)  # the tuner's file, or its bare table
+        for name, classes in table.items():
+            kt = _KEY_TYPE_NAMES.get(name)
+            if kt is None:
+                raise ValueError("DFR_TUNE_FILE %s: unknown key type %r" % (path, name))
+            for c, entry in classes.items():
+                try:
+                    t = dfr_tune_t(*(int(entry.get(f, 0) if f == "schedule" else entry[f]) for f in TUNE_FIELDS))
+                    c = int(c)
+                except (KeyError, TypeError, ValueError, AttributeError) as e:
+                    raise ValueError("DFR_TUNE_FILE %s: entry %s / class %s: %r" % (path, name, c, e)) from None
+                rc = lib.dfr_tune_set(kt, c, ctypes.byref(t))
+                if rc != DFR_OK:  # (the text comes from this handle: load() holds its lock)
+                    raise DfrError(rc, "DFR_TUNE_FILE %s: entry %s / class %s" % (path, name, c),
+                                   lib.dfr_status_string(rc).decode())
+    spin = os.environ.get("DFR_SPIN_LIMIT")
+    if spin:
+        limit = int(spin)
+        if not 0 <= limit < (1 << 32):
+            raise ValueError("DFR_SPIN_LIMIT must be an integer in [0, 2^32), not %r" % spin)
+        rc = lib.dfr_set_debug(limit, 0)
+        if rc != DFR_OK:
+            raise DfrError(rc, "DFR_SPIN_LIMIT", lib.dfr_status_string(rc).decode())
 
 
 def _status_text(code: int) -> str:
