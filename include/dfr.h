@@ -58,7 +58,8 @@ enum dfr_status {
     DFR_ERR_OVER_BUDGET = 5,  /* a served request exceeds the server's memory budget */
     DFR_ERR_BUSY = 6,         /* the server cannot take the request now */
     DFR_ERR_BOUNDS = 7,       /* a device-side bounds check rejected a write (result invalid) */
-    DFR_ERR_TOO_LARGE = 8     /* more keys than dfr_sort_u32_noalloc's fixed scratch holds */
+    DFR_ERR_TOO_LARGE = 8,    /* more keys than dfr_sort_u32_noalloc's fixed scratch holds */
+    DFR_ERR_HOST = 9          /* a host resource (a thread, host memory) could not be obtained */
 };
 
 enum dfr_key_type {
@@ -165,16 +166,25 @@ int dfr_get_stats(const void* ws, dfr_stream_t stream, dfr_stats_t* out);
  * that loads the library holds until the process exits.
  *   keys  [n] device, in/out;  n <= DFR_NOALLOC_MAX_N.
  * Returns DFR_ERR_TOO_LARGE for n > DFR_NOALLOC_MAX_N (nothing enqueued),
- * DFR_ERR_INVALID_ARG for a null or misaligned `keys`, DFR_ERR_CUDA if the
- * launch or the one-time set-up fails.  It calls no cudaMalloc, no cudaFree
- * and no allocating library routine.
+ * DFR_ERR_INVALID_ARG for a null or misaligned `keys` or keys inside the
+ * fixed array, DFR_ERR_CUDA if the launch or the one-time set-up fails (a
+ * failed set-up is retried by the next call).  It calls no cudaMalloc, no
+ * cudaFree and no allocating library routine.
  * The first call on a device (with that device current) resolves the fixed
  * array's device address; make that first call before any stream capture.
  * Every call on a device shares the one array, which keeps the previous
  * call's contents; the call clears what must start at zero itself.  Calls
  * whose work overlaps on the GPU (other streams, other host threads) race on
- * the array: serialise them.  Device-side errors of this call are not
- * reported (there is no caller-visible workspace to hold the status word).
+ * the array: serialise them.
+ * Device-side status: there is no caller-visible workspace, so the device
+ * status word of this call cannot be read back.  For u32 key-only arrays of
+ * at most DFR_NOALLOC_MAX_N keys the launch sequence contains no device-side
+ * wait (tiles claim bucket runs with atomics; the look-back of the LSD
+ * schedules only serves larger arrays), so DFR_ERR_TIMEOUT cannot arise, and
+ * the bounds and queue-capacity checks fail only after an internal fault.  If
+ * one did fail, the keys would be left unsorted with nothing reported:
+ * callers that must see the device status use dfr_sort_u32 with their own
+ * workspace and dfr_last_device_status().
  */
 #define DFR_NOALLOC_MAX_N ((uint64_t)1u << 20)
 int dfr_sort_u32_noalloc(uint32_t* keys, uint64_t n, dfr_stream_t stream);
@@ -285,7 +295,9 @@ typedef struct dfr_server dfr_server_t;
 
 /* dfr_server_create -- a server on `device` owning `mem_budget_bytes` of
  * device memory (allocated here, >= 4096) with `n_streams` streams (1 ..
- * DFR_SERVER_MAX_STREAMS).  DFR_ERR_CUDA if an allocation fails. */
+ * DFR_SERVER_MAX_STREAMS).  DFR_ERR_CUDA if a device allocation or stream
+ * fails; DFR_ERR_HOST if host memory or the dispatcher thread cannot be had
+ * (everything created so far is released; *server stays NULL). */
 int dfr_server_create(dfr_server_t** server, int device, size_t mem_budget_bytes, int n_streams);
 
 /* dfr_submit -- queue one request (`req` is copied) and return its ticket.
@@ -321,14 +333,15 @@ int dfr_server_set_limits(dfr_server_t* server, uint32_t max_batch, uint32_t max
  * While pending: *done = 0 and DFR_OK.  An unknown or released ticket gives
  * DFR_ERR_INVALID_ARG.
  *
- * A ticket has one consumer: the server's calls may come from any threads,
- * but one ticket is polled or waited on by one thread at a time (a second
- * thread's dfr_wait on a ticket that another thread's call releases reads a
- * freed request). */
+ * Any thread may poll or wait on any ticket.  A ticket is released once:
+ * when several threads poll or wait on the same ticket, the first one to see
+ * it done gets its status and latency, and the others get
+ * DFR_ERR_INVALID_ARG (released ticket). */
 int dfr_poll(dfr_server_t* server, uint64_t ticket, int* done, double* latency_us);
 
-/* dfr_wait -- block until the request is done; then as dfr_poll (one
- * consumer per ticket, as there). */
+/* dfr_wait -- block until the request is done; then as dfr_poll.  A wait
+ * whose ticket another thread releases meanwhile returns
+ * DFR_ERR_INVALID_ARG. */
 int dfr_wait(dfr_server_t* server, uint64_t ticket, double* latency_us);
 
 /* dfr_server_stats -- batches launched so far, requests pending and batches

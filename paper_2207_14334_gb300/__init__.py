@@ -35,6 +35,7 @@ DFR_ERR_OVER_BUDGET = 5
 DFR_ERR_BUSY = 6
 DFR_ERR_BOUNDS = 7
 DFR_ERR_TOO_LARGE = 8
+DFR_ERR_HOST = 9
 
 DFR_U32 = 0
 DFR_U64 = 1

@@ -436,6 +436,7 @@ const char* dfr_status_string(int status) {
     case DFR_ERR_BUSY: return "busy";
     case DFR_ERR_BOUNDS: return "device-side bounds check failed";
     case DFR_ERR_TOO_LARGE: return "more keys than the fixed no-allocation scratch holds";
+    case DFR_ERR_HOST: return "host resource (thread or host memory) unavailable";
     default: return "unknown status";
   }
 }

@@ -41,8 +41,7 @@ constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 struct NoAllocDevice {
-  bool ready;
-  int status;
+  bool ready;           // set-up succeeded on this device (a failed set-up is retried by the next call)
   unsigned char* base;  // device address of g_noalloc_scratch on this device
   Grids grids;
   int sms;
@@ -96,11 +95,18 @@ extern "C" int dfr_sort_u32_noalloc(uint32_t* keys, uint64_t n, dfr_stream_t str
   {
     std::lock_guard<std::mutex> g(g_noalloc_mu);
     if (!d->ready) {
-      d->status = setup(dev, d);
+      const int rc = setup(dev, d);
+      if (rc != DFR_OK) {
+        // Leave the device un-set-up so that a later call retries (the failure
+        // may be transient, e.g. a first call made inside a stream capture),
+        // and take back the non-sticky error the failed runtime call left, so
+        // that the caller's next cudaGetLastError does not report it.
+        cudaGetLastError();
+        return rc;
+      }
       d->ready = true;
     }
   }
-  if (d->status != DFR_OK) return d->status;
   cudaStream_t st = (cudaStream_t)stream;
 
   // scratch buffer first, then the workspace (both 256-byte aligned)

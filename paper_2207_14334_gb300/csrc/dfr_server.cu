@@ -23,11 +23,13 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <new>
 #include <thread>
 #include <unordered_map>
 #include <vector>
 
 #include "dfr_host.cuh"
+#include "dfr_tickets.h"
 
 namespace dfr {
 namespace {
@@ -321,30 +323,41 @@ int dfr_server_create(dfr_server_t** out, int device, size_t mem_budget_bytes, i
   *out = nullptr;
   if (mem_budget_bytes < 4096 || n_streams < 1 || n_streams > DFR_SERVER_MAX_STREAMS) return DFR_ERR_INVALID_ARG;
   if (cudaSetDevice(device) != cudaSuccess) return DFR_ERR_CUDA;
-  dfr_server* s = new dfr_server();
+  dfr_server* s = new (std::nothrow) dfr_server();
+  if (!s) return DFR_ERR_HOST;
   s->device = device;
   s->budget = mem_budget_bytes & ~(size_t)255;
-  bool ok = cudaMalloc(&s->base, s->budget) == cudaSuccess;
-  const size_t nslots = (size_t)n_streams * DFR_SERVER_MAX_INFLIGHT;
-  ok = ok && cudaMallocHost(&s->status_host, nslots * kStatusSlot) == cudaSuccess;
-  for (size_t i = 0; ok && i < nslots; ++i) s->free_slots.push_back((int)(nslots - 1 - i));
-  for (int i = 0; ok && i < n_streams; ++i) {
-    cudaStream_t st;
-    ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
-    if (ok) {
-      s->streams.push_back(st);
-      s->stream_load.push_back(0u);
-    }
-  }
-  if (!ok) {
+  int rc = DFR_OK;
+  auto release = [s] {
     for (auto x : s->streams) cudaStreamDestroy(x);
     if (s->status_host) cudaFreeHost(s->status_host);
     if (s->base) cudaFree(s->base);
+    delete s->pool;
     delete s;
-    return DFR_ERR_CUDA;
+  };
+  try {
+    bool ok = cudaMalloc(&s->base, s->budget) == cudaSuccess;
+    const size_t nslots = (size_t)n_streams * DFR_SERVER_MAX_INFLIGHT;
+    ok = ok && cudaMallocHost(&s->status_host, nslots * kStatusSlot) == cudaSuccess;
+    for (size_t i = 0; ok && i < nslots; ++i) s->free_slots.push_back((int)(nslots - 1 - i));
+    for (int i = 0; ok && i < n_streams; ++i) {
+      cudaStream_t st;
+      ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+      if (ok) {
+        s->streams.push_back(st);
+        s->stream_load.push_back(0u);
+      }
+    }
+    if (!ok) rc = DFR_ERR_CUDA;
+    if (rc == DFR_OK) s->pool = new Pool(s->budget);
+  } catch (...) {  // host memory for the bookkeeping (std::bad_alloc)
+    rc = DFR_ERR_HOST;
   }
-  s->pool = new Pool(s->budget);
-  s->thread = std::thread([s] { s->run(); });
+  if (rc == DFR_OK && !start_thread(&s->thread, [s] { s->run(); }, SpawnStdThread{})) rc = DFR_ERR_HOST;
+  if (rc != DFR_OK) {
+    release();
+    return rc;
+  }
   *out = s;
   return DFR_OK;
 }
@@ -397,14 +410,13 @@ int dfr_server_set_limits(dfr_server_t* s, uint32_t max_batch, uint32_t max_infl
 int dfr_poll(dfr_server_t* s, uint64_t ticket, int* done, double* latency_us) {
   if (!s || !done) return DFR_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
-  auto it = s->requests.find(ticket);
-  if (it == s->requests.end()) return DFR_ERR_INVALID_ARG;
-  Request* r = it->second;
-  *done = r->done ? 1 : 0;
-  if (!r->done) return DFR_OK;
+  Request* r = nullptr;
+  const Ticket t = take_if_done(s->requests, ticket, &r);
+  *done = t == Ticket::done ? 1 : 0;
+  if (t == Ticket::unknown) return DFR_ERR_INVALID_ARG;
+  if (t == Ticket::pending) return DFR_OK;
   if (latency_us) *latency_us = r->latency_us;
   const int st = r->status;
-  s->requests.erase(it);
   delete r;
   return st;
 }
@@ -412,13 +424,10 @@ int dfr_poll(dfr_server_t* s, uint64_t ticket, int* done, double* latency_us) {
 int dfr_wait(dfr_server_t* s, uint64_t ticket, double* latency_us) {
   if (!s) return DFR_ERR_INVALID_ARG;
   std::unique_lock<std::mutex> lk(s->mu);
-  auto it = s->requests.find(ticket);
-  if (it == s->requests.end()) return DFR_ERR_INVALID_ARG;
-  Request* r = it->second;
-  while (!r->done) s->cv.wait_for(lk, std::chrono::milliseconds(1));
+  Request* r = nullptr;
+  if (wait_and_take(lk, s->cv, s->requests, ticket, &r) != Ticket::done) return DFR_ERR_INVALID_ARG;
   if (latency_us) *latency_us = r->latency_us;
   const int st = r->status;
-  s->requests.erase(ticket);
   delete r;
   return st;
 }
