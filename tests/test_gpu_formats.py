@@ -86,3 +86,30 @@ def test_batch_formats(dfr):
     assert dfr.dfr_last_device_status(ws) == dfr.DFR_OK
     for a, d in zip(arrays, dk):
         assert np.array_equal(dfr.to_numpy(d, np.uint32), oracle.sort_format(0, 0x102, a))
+
+
+def test_plain_format_call_ignores_a_stale_descriptor_table(dfr):
+    """The key-format pre-pass of a plain call runs before the call's first
+    kernel writes the array descriptor into the workspace, so it must take the
+    descriptor from its launch parameters.  Here the workspace still holds the
+    descriptor of a decoy array, left by a one-array batch call (same table
+    slot), and the decoy stays allocated: reading the stale table would map
+    the decoy's keys instead of the real ones (a wrong result and a changed
+    decoy, no stray access).  Both must come out right."""
+    import torch
+
+    decoy = _keys(4, 0, 300_000, 4001)
+    real = _keys(4, 1, 100_003, 4002)
+    dd = dfr.to_device(decoy)
+    db = torch.empty_like(dd)
+    s = dfr.Sorter(dfr.DFR_U32, 300_000)
+    segs = [(dfr.DFR_U32, dd, 0, db, 0, decoy.size)]
+    assert dfr.dfr_sort_batch(segs, s.ws, s.ws_bytes) == dfr.DFR_OK
+    assert dfr.dfr_last_device_status(s.ws) == dfr.DFR_OK
+    sorted_decoy = dfr.to_numpy(dd, np.uint32)
+    assert np.array_equal(sorted_decoy, oracle.sort_u32(decoy))
+    dr = dfr.to_device(real)
+    s.sort_(dr, None, real.size, key_format=dfr.DFR_FMT_SIGNED)
+    assert s.device_status() == dfr.DFR_OK
+    assert np.array_equal(dfr.to_numpy(dr, np.uint32), oracle.sort_format(0, 1, real))
+    assert np.array_equal(dfr.to_numpy(dd, np.uint32), sorted_decoy)
