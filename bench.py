@@ -41,12 +41,12 @@ if ROOT not in sys.path:
 
 import synth  # noqa: E402
 
-# ncu DRAM traffic of the u32 key-only scatter kernel (read + write bytes per
-# key dealt), from profiles/k_scatter_u32_uniform_2^26.md; valid only for u32
-# key-only workloads while the kernel sources hash to SCATTER_SRC_SHA (else
-# the roofline's traffic is reported as null).
-SCATTER_NCU_BYTES_PER_KEY = 7.140
-SCATTER_SRC_SHA = "07c963dfd0f1f19e"
+# ncu DRAM traffic figures (read + write bytes per key the kernel handles) of
+# the u32 key-only kernels, kept in profiles/traffic.json with the sha256 of
+# each kernel's own source file at the time of the capture; a figure whose
+# source has changed since is not used (the roofline's traffic is then null).
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
 
 WORKLOADS = {
     "plain_u32_2^28": dict(kind="plain", key="u32", n=1 << 28, dists=list(synth.U32_DISTRIBUTIONS)),
@@ -65,14 +65,27 @@ SEED_OFFSET = {"plain_u32_2^28": 20, "plain_u32_1M": 1, "kv_u64_2^27": 30, "plai
                "batch_u32_4096": 40, "served_mixed": 50}
 
 
-def kernel_source_sha() -> str:
+def source_sha(paths) -> str:
+    """sha256 (first 16 hex digits) of the files `paths` (relative to the
+    repository root), concatenated in the order given."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2207_14334_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def traffic_per_key(kernel: str):
+    """The ncu DRAM bytes per key of `kernel` for u32 key-only sorts, or None
+    when no capture matches the kernel's current source."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            entry = json.load(f).get(kernel)
+        if entry and source_sha(entry["source"]) == entry["source_sha16"]:
+            return float(entry["dram_bytes_per_key"])
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    return None
 
 
 def measured_peaks():
@@ -361,7 +374,7 @@ def batch_inputs(wl):
     return arrays, kinds
 
 
-def run_batch(args, wl, dfr, dev, world, rank):
+def run_batch(args, wl, dfr, dev, world, rank, emit=True):
     """Many arrays: one dfr_sort_batch launch sequence against one plain
     dfr_sort_u32 call per array on one stream, uncaptured and captured in a
     CUDA graph.  Every arm sorts the same arrays, restored from a pristine copy
@@ -488,7 +501,7 @@ def run_batch(args, wl, dfr, dev, world, rank):
                "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": int(host.nbytes), "ms_per_step": ems}
 
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
         cpu = cpu_batch_time(arrays, args.cpu_sample)
     if rank == 0:
         line = {
@@ -512,8 +525,10 @@ def run_batch(args, wl, dfr, dev, world, rank):
             "plan": {k: stats[k] for k in ("levels", "cta_keys", "wsort_keys", "tiny_keys", "const_keys",
                                            "cta_buckets", "wsort_buckets", "model_bytes")},
         }
-        print(json.dumps(line), flush=True)
-    return 0
+        if emit:
+            print(json.dumps(line), flush=True)
+        return line
+    return None
 
 
 def cpu_batch_time(arrays, sample_keys):
@@ -772,50 +787,12 @@ def config_of(name, wl):
             "inputs": "restored from a pristine device copy before every sort (untimed)"}
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="dfr", choices=["dfr", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-sample", type=int, default=1 << 26)
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-streams", type=int, default=3, help="streams (device buffer sets) of the end-to-end leg")
-    ap.add_argument("--dists", default="", help="comma-separated subset of the workload's distributions")
-    ap.add_argument("--requests", type=int, default=0, help="served workload: requests per pass")
-    ap.add_argument("--serve-streams", type=int, default=4, help="served workload: server streams")
-    ap.add_argument("--schedule", default="plan", choices=["plan", "msd", "lsd", "dfr"],
-                    help="plain workloads: override the launch plan's schedule of the top digits "
-                         "(msd: diverting MSD; lsd: diverting LSD with one counting read; dfr: diverting "
-                         "LSD with the estimated first deal, Fast Radix)")
-    args = ap.parse_args()
-    wl = dict(WORKLOADS[args.workload])
-    if args.dists and "dists" in wl:
-        wl["dists"] = [d for d in args.dists.split(",") if d in wl["dists"]]
-    rank, world, local = dist_setup()
-
-    if args.impl == "reference":
-        return run_reference(args, wl, world, rank)
-
+def run_plain(args, wl, dfr, dev, world, rank, emit=True):
+    """One plain-sort workload (every array sorted alone, timed with CUDA
+    events); returns rank 0's JSON line (printed when `emit`)."""
     import torch
 
-    import __graft_entry__
-
-    if world > 1:
-        import torch.distributed as tdist
-
-        torch.cuda.set_device(local)
-        tdist.init_process_group("nccl")
-    __graft_entry__.build()
-    import paper_2207_14334_gb300 as dfr
-
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    if wl["kind"] == "batch":
-        return run_batch(args, wl, dfr, dev, world, rank)
-    if wl["kind"] == "served":
-        return run_served(args, wl, dfr, dev, world, rank)
+    local = dev.index or 0
     stream = torch.cuda.current_stream(dev)
     n = wl["n"]
     kv = wl["key"] == "u64kv"
@@ -918,18 +895,21 @@ def main():
     # dealt, per launch).
     scatter_keys = sum(sum(p["level_keys"]) for p in plan.values())
     lsd_keys = sum(p["lsd_keys"] for p in plan.values())
-    scatter_ms, scatter_launches = prof["scatter"]
-    lsd_ms, lsd_launches = prof.get("lsd_pass", (0.0, 0))
-    if lsd_ms > scatter_ms:
-        dom_kernel, dom_ms, dom_launches, dom_keys = "k_lsd_pass", lsd_ms, lsd_launches, lsd_keys
-    else:
-        dom_kernel, dom_ms, dom_launches, dom_keys = "k_scatter", scatter_ms, scatter_launches, scatter_keys
+    # The dominant record-moving kernel: the MSD levels' scatter, the LSD
+    # passes (when an LSD schedule dealt the top digits) or the CTA sort --
+    # algorithmic bytes = a read and a write of every record it handles.
+    cta_keys = sum(p["cta_keys"] for p in plan.values())
+    cands = {"k_scatter": ("scatter", scatter_keys), "k_lsd_pass": ("lsd_pass", lsd_keys),
+             "k_ctasort": ("ctasort", cta_keys)}
+    dom_kernel = max((k for k in cands if cands[k][0] in prof), key=lambda k: prof[cands[k][0]][0])
+    dom_ms, dom_launches = prof[cands[dom_kernel][0]]
+    dom_keys = cands[dom_kernel][1]
     dom_bytes = 2 * rec * dom_keys
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else 0.0
     traffic = None
-    if (SCATTER_NCU_BYTES_PER_KEY is not None and not kv and dom_kernel == "k_scatter"
-            and SCATTER_SRC_SHA == kernel_source_sha()):
-        traffic = SCATTER_NCU_BYTES_PER_KEY * scatter_keys / max(1, scatter_launches)
+    per_key = traffic_per_key(dom_kernel) if not kv else None
+    if per_key is not None:
+        traffic = per_key * dom_keys / max(1, dom_launches)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": dom_kernel,
                 "peak_source": peak_kind,
@@ -1030,7 +1010,7 @@ def main():
                           "overlap" % ns}
 
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
         sample_n = min(n, args.cpu_sample)
         ck, cdt = cpu_oracle_time(inputs, sample_n, wl["key"])
         cpu = {"value": ck / cdt / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
@@ -1046,7 +1026,87 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "per_dist": per_dist, "kernels": kernel_share,
         }
-        print(json.dumps(line), flush=True)
+        if emit:
+            print(json.dumps(line), flush=True)
+        return line
+    return None
+
+
+def extra_summary(line):
+    """The parts of another workload's line carried in the default line."""
+    if line is None:
+        return None
+    keep = ("metric", "value", "unit", "ms_per_step", "config", "roofline", "clocks", "gpu_launches",
+            "batched_vs_plain", "sort_roofline_frac")
+    out = {k: line[k] for k in keep if k in line}
+    if "per_dist" in line:
+        out["per_dist"] = {d: {k: v[k] for k in ("ms", "gkeys_s", "sort_roofline_frac", "schedule") if k in v}
+                           for d, v in line["per_dist"].items()}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dfr", choices=["dfr", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-sample", type=int, default=1 << 26)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: leave out the 2^27 key-value and 4096-array batch results")
+    ap.add_argument("--e2e-streams", type=int, default=3, help="streams (device buffer sets) of the end-to-end leg")
+    ap.add_argument("--dists", default="", help="comma-separated subset of the workload's distributions")
+    ap.add_argument("--requests", type=int, default=0, help="served workload: requests per pass")
+    ap.add_argument("--serve-streams", type=int, default=4, help="served workload: server streams")
+    ap.add_argument("--schedule", default="plan", choices=["plan", "msd", "lsd", "dfr"],
+                    help="plain workloads: override the launch plan's schedule of the top digits "
+                         "(msd: diverting MSD; lsd: diverting LSD with one counting read; dfr: diverting "
+                         "LSD with the estimated first deal, Fast Radix)")
+    args = ap.parse_args()
+    wl = dict(WORKLOADS[args.workload])
+    if args.dists and "dists" in wl:
+        wl["dists"] = [d for d in args.dists.split(",") if d in wl["dists"]]
+    rank, world, local = dist_setup()
+
+    if args.impl == "reference":
+        return run_reference(args, wl, world, rank)
+
+    import torch
+
+    import __graft_entry__
+
+    if world > 1:
+        import torch.distributed as tdist
+
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    __graft_entry__.build()
+    import paper_2207_14334_gb300 as dfr
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if wl["kind"] == "batch":
+        run_batch(args, wl, dfr, dev, world, rank)
+        return 0
+    if wl["kind"] == "served":
+        return run_served(args, wl, dfr, dev, world, rank)
+    if wl["kind"] == "plain" and args.workload == DEFAULT_WORKLOAD and not args.no_extras:
+        line = run_plain(args, wl, dfr, dev, world, rank, emit=False)
+        extra = argparse.Namespace(**vars(args))
+        extra.steps, extra.warmup, extra.no_e2e, extra.cpu_sample = 3, 3, True, 0
+        extra.dists = ""
+        extra.workload = "kv_u64_2^27"
+        kv_line = run_plain(extra, dict(WORKLOADS[extra.workload]), dfr, dev, world, rank, emit=False)
+        extra.workload = "batch_u32_4096"
+        b_line = run_batch(extra, dict(WORKLOADS[extra.workload]), dfr, dev, world, rank, emit=False)
+        if rank == 0:
+            line["kv_u64_2^27"] = extra_summary(kv_line)
+            line["batch_u32_4096"] = extra_summary(b_line)
+            print(json.dumps(line), flush=True)
+    else:
+        run_plain(args, wl, dfr, dev, world, rank)
     if world > 1:
         import torch.distributed as tdist
 

@@ -59,6 +59,16 @@ constexpr int MAXLV = 12;     // control blocks per level (>= launched levels + 
 constexpr int EXTRA_LEVELS = 2;  // levels launched beyond key bits / RB (room for narrow windows)
 constexpr uint32_t T_WARP = 32;  // tiny-bucket threshold (warp sort)
 
+struct NoVal {};
+// u32 key-only sorts have two CTA sorts: k_ctasort32 for buckets whose keys
+// vary in at most CTA32_SPAN bits (the usual case), the general k_ctasort
+// (second queue) for the rest; the classifiers route by a bound on the span.
+constexpr uint32_t CTA32_SPAN = 16;
+template <class K, class V>
+constexpr bool two_cta_queues() {
+  return std::is_same<K, uint32_t>::value && std::is_same<V, NoVal>::value;
+}
+
 enum : uint32_t { DERR_TIMEOUT = 1u, DERR_BOUNDS = 2u, DERR_CAPACITY = 4u };
 enum : uint32_t {
   ERR_SITE_SCATTER_STAGE = 1u, ERR_SITE_SCATTER_WRITE, ERR_SITE_CTASORT_STAGE, ERR_SITE_WARPSORT_STAGE,
@@ -69,8 +79,6 @@ constexpr uint32_t NO_OWNER = 0xffffffffu;  // tile-owner entry of a tile that m
 // already dealt on its window (k_classify only classifies its buckets).
 enum : uint32_t { SEG_NEEDS_HIST = 1u, SEG_NEEDS_ANDOR = 2u, SEG_PREDEALT = 4u };
 enum : uint32_t { ITEM_PARITY = 1u, ITEM_COPY = 2u };
-
-struct NoVal {};
 
 // One array to sort (one per batch entry; a plain call has one).
 struct ArrDesc {
@@ -137,6 +145,8 @@ struct Ctl {
   uint32_t val_bytes;
   uint32_t wq_count;
   uint32_t wq_claim;
+  uint32_t cta2_count;  // u32 key-only: buckets the fast CTA sort handed to the general one
+  uint32_t cta2_claim;
   unsigned long long n_total;
   unsigned long long cta_buckets, cta_keys;
   unsigned long long wsort_buckets, wsort_keys;
@@ -197,6 +207,7 @@ struct Ctx {
   uint32_t* tile_owner;
   uint32_t* status;   // key-value sorts: [tilecap][M] look-back words
   Item* cta_q;
+  Item* cta_q2;       // u32 key-only: buckets for the general CTA sort (capacity ctacap)
   Item* w_q;          // buckets for the warp sort
   CopyItem* copy_q;
   uint32_t* copy_owner;
@@ -806,9 +817,14 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
     if (n <= (uint32_t)TCTA) {
       if (threadIdx.x == 0) {
         const bool small = n <= c.warp_max;
-        const uint32_t q = atomicAdd(small ? &ctl->wq_count : &ctl->cta_count, 1u);
+        // keys varying in more bits than k_ctasort32 sorts go to the general CTA sort
+        const K vmk = orv ^ andv;
+        const bool wide =
+            two_cta_queues<K, V>() && (uint32_t)(top_bit<K>(vmk) - low_bit<K>(vmk) + 1) > CTA32_SPAN;
+        uint32_t* qc = small ? &ctl->wq_count : (wide ? &ctl->cta2_count : &ctl->cta_count);
+        const uint32_t q = atomicAdd(qc, 1u);
         if (q < (small ? c.wqcap : c.ctacap)) {
-          (small ? c.w_q : c.cta_q)[q] = Item{0u, n, a, 0u};
+          (small ? c.w_q : (wide ? c.cta_q2 : c.cta_q))[q] = Item{0u, n, a, 0u};
           atomicAdd(small ? &ctl->wsort_buckets : &ctl->cta_buckets, 1ull);
           atomicAdd(small ? &ctl->wsort_keys : &ctl->cta_keys, (unsigned long long)n);
         } else {
@@ -1007,12 +1023,12 @@ __device__ __forceinline__ void adapt_note(TileDigits& a, uint32_t tcount, uint3
 }
 
 // Rank the key-only items of one tile: item i = VK*q + u of thread x is
-// element VK*(q*NT + x) + u, elements [vlo, vhi) are valid; r[i] = a
-// distinct slot of the key's digit on the counters cnt.  Every thread of the
-// block calls it.
-template <class K, int NT, int KPT>
-__device__ __forceinline__ void rank_keys(const K (&k)[KPT], uint32_t (&r)[KPT], uint32_t shift, uint32_t vlo,
-                                          uint32_t vhi, uint32_t* cnt, const TileDigits& a) {
+// element VK*(q*NT + x) + u, elements [vlo, vhi) are valid; put(i, rank)
+// receives a distinct slot of the key's digit on the counters cnt (0 for an
+// invalid item).  Every thread of the block calls it.
+template <class K, int NT, int KPT, class Put>
+__device__ __forceinline__ void rank_keys_to(const K (&k)[KPT], Put&& put, uint32_t shift, uint32_t vlo,
+                                             uint32_t vhi, uint32_t* cnt, const TileDigits& a) {
   constexpr uint32_t VK = 16 / sizeof(K);
   const uint32_t lane = lane_id();
   if (a.run) {
@@ -1035,12 +1051,12 @@ __device__ __forceinline__ void rank_keys(const K (&k)[KPT], uint32_t (&r)[KPT],
         if (lane == 0) base = atomicAdd(&cnt[dfirst], 32u * VK);
         base = __shfl_sync(FULL, base, 0) + lane * VK;
 #pragma unroll
-        for (int u = 0; u < (int)VK; ++u) r[q * VK + u] = base + (uint32_t)u;
+        for (int u = 0; u < (int)VK; ++u) put(q * VK + u, base + (uint32_t)u);
       } else {
 #pragma unroll
         for (int u = 0; u < (int)VK; ++u) {
           const uint32_t e = e0 + (uint32_t)u;
-          r[q * VK + u] = (e >= vlo && e < vhi) ? atomicAdd(&cnt[digit_of(k[q * VK + u], shift)], 1u) : 0u;
+          put(q * VK + u, (e >= vlo && e < vhi) ? atomicAdd(&cnt[digit_of(k[q * VK + u], shift)], 1u) : 0u);
         }
       }
     }
@@ -1060,15 +1076,22 @@ __device__ __forceinline__ void rank_keys(const K (&k)[KPT], uint32_t (&r)[KPT],
         if ((int)lane == leader) base = atomicAdd(&cnt[dom], (uint32_t)__popc(m));
         base = __shfl_sync(FULL, base, leader);
       }
-      r[i] = isdom ? base + (uint32_t)__popc(m & lt) : (valid ? atomicAdd(&cnt[d], 1u) : 0u);
+      put(i, isdom ? base + (uint32_t)__popc(m & lt) : (valid ? atomicAdd(&cnt[d], 1u) : 0u));
     }
   } else {
 #pragma unroll
     for (int i = 0; i < KPT; ++i) {
       const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
-      r[i] = (e >= vlo && e < vhi) ? atomicAdd(&cnt[digit_of(k[i], shift)], 1u) : 0u;
+      put(i, (e >= vlo && e < vhi) ? atomicAdd(&cnt[digit_of(k[i], shift)], 1u) : 0u);
     }
   }
+}
+
+// As rank_keys_to, with the ranks in r[].
+template <class K, int NT, int KPT>
+__device__ __forceinline__ void rank_keys(const K (&k)[KPT], uint32_t (&r)[KPT], uint32_t shift, uint32_t vlo,
+                                          uint32_t vhi, uint32_t* cnt, const TileDigits& a) {
+  rank_keys_to<K, NT, KPT>(k, [&](int i, uint32_t v) { r[i] = v; }, shift, vlo, vhi, cnt, a);
 }
 
 // Decoupled look-back for digit d of tile t (one thread per digit): sums the
@@ -1322,7 +1345,8 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
   __shared__ uint32_t s_new_owner[M], s_new_zero[M], s_new_ts[M], s_new_nt[M], s_new_copy[M];
   __shared__ unsigned long long s_stat[10];
   __shared__ uint32_t s_bcnt[M], s_boff[M], s_run_off[M], s_run_len[M];
-  __shared__ uint32_t s_nrun, s_qn[2], s_qbase[2];
+  __shared__ uint32_t s_nrun, s_qn[3], s_qbase[3];
+  __shared__ uint32_t s_run_top[M];  // bound on each run's highest varying bit + 1
   Ctl* ctl = c.ctl;
   const uint32_t nseg = min(ctl->lv[L].nseg, c.segcap);
   const Seg* segs = ((L & 1) ? c.segs[1] : c.segs[0]);
@@ -1450,30 +1474,35 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
         s_boff[d] = off;
         __syncthreads();
         if (threadIdx.x == 0) {
-          uint32_t nr = 0, roff = 0, rlen = 0;
+          // (a run of one bucket varies below the window; one of several
+          // buckets also in the window bits where their digits differ)
+          uint32_t nr = 0, roff = 0, rlen = 0, dfirst = 0, dlast = 0;
+          auto close = [&]() {
+            s_run_off[nr] = roff;
+            s_run_len[nr] = rlen;
+            s_run_top[nr] = seg.shift + (dfirst == dlast ? 0u : 32u - (uint32_t)__clz((int)(dfirst ^ dlast)));
+            ++nr;
+          };
           for (uint32_t x = 0; x < (uint32_t)M; ++x) {
             const uint32_t cx = s_bcnt[x];
             if (cx == 0u) continue;
             if (cx == 0xffffffffu || rlen + cx > (uint32_t)TCTA) {
-              if (rlen) {
-                s_run_off[nr] = roff;
-                s_run_len[nr] = rlen;
-                ++nr;
-              }
+              if (rlen) close();
               rlen = 0;
               if (cx == 0xffffffffu) continue;
             }
-            if (rlen == 0) roff = s_boff[x];
+            if (rlen == 0) {
+              roff = s_boff[x];
+              dfirst = x;
+            }
+            dlast = x;
             rlen += cx;
           }
-          if (rlen) {
-            s_run_off[nr] = roff;
-            s_run_len[nr] = rlen;
-            ++nr;
-          }
+          if (rlen) close();
           s_nrun = nr;
           s_qn[0] = 0;
           s_qn[1] = 0;
+          s_qn[2] = 0;
         }
         __syncthreads();
         const uint32_t nr = s_nrun;
@@ -1517,8 +1546,10 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
             atomicAdd(&s_stat[8], 1ull);
             atomicAdd(&s_stat[7], (unsigned long long)rlen);
           } else {
-            rcls = 4;
-            rloc = atomicAdd(&s_qn[1], 1u);
+            // a run whose keys may vary in more bits than k_ctasort32 sorts
+            // goes to the general CTA sort's queue
+            rcls = (two_cta_queues<K, V>() && s_run_top[threadIdx.x] > CTA32_SPAN) ? 5 : 4;
+            rloc = atomicAdd(&s_qn[rcls - 3], 1u);
             atomicAdd(&s_stat[5], 1ull);
             atomicAdd(&s_stat[6], (unsigned long long)rlen);
           }
@@ -1532,12 +1563,14 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
         if (threadIdx.x == 0) {
           s_qbase[0] = s_qn[0] ? atomicAdd(&ctl->wq_count, s_qn[0]) : 0u;
           s_qbase[1] = s_qn[1] ? atomicAdd(&ctl->cta_count, s_qn[1]) : 0u;
+          s_qbase[2] = s_qn[2] ? atomicAdd(&ctl->cta2_count, s_qn[2]) : 0u;
         }
         __syncthreads();
         if (rcls >= 3) {
           const uint32_t q = s_qbase[rcls - 3] + rloc;
+          Item* qa = rcls == 3 ? c.w_q : (rcls == 4 ? c.cta_q : c.cta_q2);
           if (q < (rcls == 3 ? c.wqcap : c.ctacap))
-            (rcls == 3 ? c.w_q : c.cta_q)[q] = Item{roff, rlen, seg.arr, pout | (rcopy ? ITEM_COPY : 0u)};
+            qa[q] = Item{roff, rlen, seg.arr, pout | (rcopy ? ITEM_COPY : 0u)};
           else
             atomicOr(&ctl->err, DERR_CAPACITY);
         }
@@ -1960,8 +1993,10 @@ constexpr int ctasort_min_blocks() {
   return NT >= 1024 ? 1 : ((std::is_same<V, NoVal>::value && sizeof(K) == 4) ? 3 : 2);
 }
 
+// `second`: sort the second queue (buckets the u32 key-only fast CTA sort
+// handed over) instead of the classifier's queue.
 template <class K, class V, int NT, int KPT>
-__global__ void __launch_bounds__(NT, (ctasort_min_blocks<K, V, NT>())) k_ctasort(Ctx c) {
+__global__ void __launch_bounds__(NT, (ctasort_min_blocks<K, V, NT>())) k_ctasort(Ctx c, int second) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr uint32_t CAP = (uint32_t)NT * KPT;
   constexpr int NW = NT / 32;
@@ -1980,18 +2015,20 @@ __global__ void __launch_bounds__(NT, (ctasort_min_blocks<K, V, NT>())) k_ctasor
   __shared__ uint32_t s_q, s_maxc, s_mixed;
   __shared__ unsigned long long s_orv[2];
   Ctl* ctl = c.ctl;
-  const uint32_t count = min(ctl->cta_count, c.ctacap);
+  const uint32_t count = min(second ? ctl->cta2_count : ctl->cta_count, c.ctacap);
+  uint32_t* claim = second ? &ctl->cta2_claim : &ctl->cta_claim;
+  const Item* queue = second ? c.cta_q2 : c.cta_q;
 
   for (;;) {
     if (threadIdx.x == 0) {
-      s_q = atomicAdd(&ctl->cta_claim, 1u);
+      s_q = atomicAdd(claim, 1u);
       s_orv[0] = 0ull;
       s_orv[1] = 0ull;
     }
     __syncthreads();
     const uint32_t q = s_q;
     if (q >= count) break;
-    const Item it = c.cta_q[q];
+    const Item it = queue[q];
     const ArrDesc ad = c.arrs[it.arr];
     const bool par = (it.info & ITEM_PARITY) != 0u;
     const K* src = reinterpret_cast<const K*>(par ? ad.buf : ad.keys);

@@ -12,8 +12,10 @@
 #include <vector>
 
 #include "dfr.h"
+#include "dfr_ctasort32.cuh"
 #include "dfr_device.cuh"
 #include "dfr_lsd.cuh"
+#include "dfr_scatter_bulk.cuh"
 
 namespace dfr {
 
@@ -98,7 +100,8 @@ inline int geometry_of(uint64_t ntot, uint32_t narr) {
 }
 
 struct Layout {
-  size_t ctl, arrs, root, segs0, segs1, hist0, hist1, cur0, cur1, owner, status, ctaq, wq, copyq, copyowner, total;
+  size_t ctl, arrs, root, segs0, segs1, hist0, hist1, cur0, cur1, owner, status, ctaq, ctaq2, wq, copyq, copyowner,
+      total;
   uint32_t segcap, tilecap, ctacap, wqcap, copycap, copytilecap;
   // LSD top phase (single arrays of at least lsd_min_n keys)
   bool has_lsd;
@@ -159,6 +162,8 @@ Layout make_layout(uint64_t ntot, uint32_t narr) {
   o = align256(o + (KV ? (size_t)l.tilecap * M * 4 : 0));
   l.ctaq = o;
   o = align256(o + (size_t)l.ctacap * sizeof(Item));
+  l.ctaq2 = o;  // u32 key-only: buckets the fast CTA sort hands to the general one
+  o = align256(o + (has_small_geometry<K, V>() ? (size_t)l.ctacap * sizeof(Item) : 0));
   l.wq = o;
   o = align256(o + (size_t)l.wqcap * sizeof(Item));
   l.copyq = o;
@@ -207,6 +212,7 @@ inline Ctx make_ctx(void* ws, const Layout& l, uint32_t narr) {
   c.tile_owner = reinterpret_cast<uint32_t*>(b + l.owner);
   c.status = reinterpret_cast<uint32_t*>(b + l.status);
   c.cta_q = reinterpret_cast<Item*>(b + l.ctaq);
+  c.cta_q2 = reinterpret_cast<Item*>(b + l.ctaq2);
   c.w_q = reinterpret_cast<Item*>(b + l.wq);
   c.copy_q = reinterpret_cast<CopyItem*>(b + l.copyq);
   c.copy_owner = reinterpret_cast<uint32_t*>(b + l.copyowner);
@@ -276,7 +282,7 @@ size_t workspace_bytes(uint64_t ntot, uint32_t narr) {
 
 // Persistent grid sizes of every kernel of one key type on one device.
 struct Grids {
-  int rc, rcl, lc, sc, cl, cs, ws, cp, kf, lp, le, rc2, lp1;
+  int rc, rcl, lc, sc, cl, cs, ws, cp, kf, lp, le, rc2, lp1, cs32;
 };
 
 // The tuning entry's CTAs-per-SM caps applied to the persistent grids.
@@ -321,7 +327,13 @@ struct Kernels {
   static constexpr auto root_count2 = k_root_count<K, SNT, TILE, true>;
   static constexpr auto root_classify = k_root_classify<K, V, TILE, TCTA, WCAP>;
   static constexpr auto level_count = k_level_count<K, !std::is_same<V, NoVal>::value, SNT, TILE>;
+  // key-only deals write each digit run's 16-byte-aligned body with one bulk
+  // copy (measured against plain stores: uniform keys alike, sorted and
+  // reverse runs 1.42 -> 1.21 ms at 2^28)
+  static constexpr bool BULK = std::is_same<V, NoVal>::value;
+  static constexpr size_t sb_smem = scatter_bulk_smem_bytes<K, SNT, SKPT>();
   static constexpr auto scatter = k_scatter<K, V, SNT, SKPT>;
+  static constexpr auto scatter_bulk = k_scatter_bulk<K, SNT, SKPT>;
   static constexpr auto classify = k_classify<K, V, TILE, TCTA, WCAP>;
   static constexpr auto ctasort = k_ctasort<K, V, CNT, CKPT>;
   static constexpr auto warpsort = k_warpsort<K, V, WPB, WKPT>;
@@ -332,6 +344,18 @@ struct Kernels {
   static constexpr auto lsd_pass1 = k_lsd_pass<K, V, SNT, SKPT, 1, false>;
   static constexpr auto lsd_mid = k_lsd_mid<K, V, TILE>;
   static constexpr auto lsd_fin = k_lsd_fin<K>;
+  // u32 key-only buckets: k_ctasort32 (CS32_NC threads x 4 * CS32_NV keys)
+  // for spans up to CTA32_SPAN bits; wider ones and heavy duplicates go to
+  // the general CTA sort through the second queue
+  static constexpr bool FAST32 = has_small_geometry<K, V>();
+  // 512 sorting threads + one producer warp, a two-bucket ring, two CTAs per
+  // SM (measured: three stages 2-3% slower)
+  static constexpr int CS32_NC = 512, CS32_NV = 3, CS32_MINB = 2, CS32_STAGES = 2;
+  static constexpr int CS32_NT = CS32_NC + 32;
+  using C32 = Cta32<CS32_NC, CS32_NV, CS32_STAGES>;
+  static_assert(!FAST32 || C32::CAP == (uint32_t)TCTA, "both CTA sorts take buckets up to the diversion threshold");
+  static constexpr size_t cs32_smem = ctasort32_smem_bytes<CS32_NC, CS32_NV, CS32_STAGES>();
+  static constexpr auto ctasort32 = k_ctasort32<CS32_NC, CS32_NV, CS32_STAGES, CS32_MINB>;
 
   // grid_of(kernel, threads, dynamic smem) -> persistent grid (or < 0 on error)
   template <class GridOf>
@@ -339,7 +363,7 @@ struct Kernels {
     g->rc = grid_of((const void*)root_count, SNT, (size_t)0);
     g->rcl = grid_of((const void*)root_classify, 256, (size_t)0);
     g->lc = grid_of((const void*)level_count, SNT, (size_t)0);
-    g->sc = grid_of((const void*)scatter, SNT, sc_smem);
+    g->sc = BULK ? grid_of((const void*)scatter_bulk, SNT, sb_smem) : grid_of((const void*)scatter, SNT, sc_smem);
     g->cl = grid_of((const void*)classify, 256, (size_t)0);
     g->cs = grid_of((const void*)ctasort, CNT, cs_smem);
     g->ws = grid_of((const void*)warpsort, WPB * 32, ws_smem);
@@ -349,7 +373,8 @@ struct Kernels {
     g->lp1 = grid_of((const void*)lsd_pass1, SNT, lp_smem);
     g->le = grid_of((const void*)lsd_est, SNT, lp_smem);
     g->rc2 = grid_of((const void*)root_count2, SNT, (size_t)0);
-    return g->rc > 0 && g->rcl > 0 && g->lc > 0 && g->sc > 0 && g->cl > 0 && g->cs > 0 && g->ws > 0 && g->cp > 0 &&
+    g->cs32 = FAST32 ? grid_of((const void*)ctasort32, CS32_NT, cs32_smem) : 1;
+    return g->cs32 > 0 && g->rc > 0 && g->rcl > 0 && g->lc > 0 && g->sc > 0 && g->cl > 0 && g->cs > 0 && g->ws > 0 && g->cp > 0 &&
            g->kf > 0 && g->lp > 0 && g->le > 0 && g->rc2 > 0 && g->lp1 > 0;
   }
 };
@@ -408,10 +433,19 @@ void enqueue_sort(const Ctx& c, const Layout& lay, const Grids& g, uint32_t narr
   const uint32_t cl_grid = min_u32(lay.segcap, (uint32_t)g.cl);
   for (int L = 0; L < T::nlev; ++L) {
     hook(PK_LEVEL_COUNT, st, [&] { T::level_count<<<lc_grid, T::SNT, 0, st>>>(c, L); });
-    hook(PK_SCATTER, st, [&] { T::scatter<<<sc_grid, T::SNT, T::sc_smem, st>>>(c, L); });
+    if constexpr (T::BULK)
+      hook(PK_SCATTER, st, [&] { T::scatter_bulk<<<sc_grid, T::SNT, T::sb_smem, st>>>(c, L); });
+    else
+      hook(PK_SCATTER, st, [&] { T::scatter<<<sc_grid, T::SNT, T::sc_smem, st>>>(c, L); });
     hook(PK_CLASSIFY, st, [&] { T::classify<<<cl_grid, 256, 0, st>>>(c, L); });
   }
-  hook(PK_CTASORT, st, [&] { T::ctasort<<<min_u32(lay.ctacap, (uint32_t)g.cs), T::CNT, T::cs_smem, st>>>(c); });
+  if constexpr (T::FAST32) {
+    hook(PK_CTASORT, st,
+         [&] { T::ctasort32<<<min_u32(lay.ctacap, (uint32_t)g.cs32), T::CS32_NT, T::cs32_smem, st>>>(c); });
+    hook(PK_CTASORT, st, [&] { T::ctasort<<<min_u32(lay.ctacap, (uint32_t)g.cs), T::CNT, T::cs_smem, st>>>(c, 1); });
+  } else {
+    hook(PK_CTASORT, st, [&] { T::ctasort<<<min_u32(lay.ctacap, (uint32_t)g.cs), T::CNT, T::cs_smem, st>>>(c, 0); });
+  }
   hook(PK_WARPSORT, st, [&] {
     T::warpsort<<<min_u32((lay.wqcap + T::WPB - 1) / T::WPB, (uint32_t)g.ws), T::WPB * 32, T::ws_smem, st>>>(c);
   });
