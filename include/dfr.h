@@ -63,10 +63,12 @@ enum dfr_status {
 };
 
 enum dfr_key_type {
-    DFR_U32 = 0,     /* uint32 keys */
-    DFR_U64 = 1,     /* uint64 keys */
-    DFR_U64_KV = 2,  /* uint64 keys with uint32 payloads */
-    DFR_U32_KV = 3   /* uint32 keys with uint32 payloads */
+    DFR_U32 = 0,       /* uint32 keys */
+    DFR_U64 = 1,       /* uint64 keys */
+    DFR_U64_KV = 2,    /* uint64 keys with uint32 payloads */
+    DFR_U32_KV = 3,    /* uint32 keys with uint32 payloads */
+    DFR_U64_KV64 = 4,  /* uint64 keys with uint64 payloads */
+    DFR_U32_KV64 = 5   /* uint32 keys with uint64 payloads */
 };
 
 /* Largest number of keys in one array (the decoupled look-back keeps 30-bit
@@ -107,6 +109,19 @@ int dfr_sort_u64_kv(uint64_t* keys, uint32_t* vals, uint64_t* kbuf, uint32_t* vb
 /* dfr_sort_u32_kv -- as dfr_sort_u64_kv for uint32 keys (DFR_U32_KV workspace). */
 int dfr_sort_u32_kv(uint32_t* keys, uint32_t* vals, uint32_t* kbuf, uint32_t* vbuf, uint64_t n,
                     void* ws, size_t ws_bytes, dfr_stream_t stream);
+
+/*
+ * dfr_sort_u64_kv64 / dfr_sort_u32_kv64 -- the same stable key-value sort with
+ * 64-bit payloads: records of the paper's statement of the problem carry
+ * data beside their key (Preliminaries), and a 64-bit payload holds a
+ * pointer, an offset into a large table or a second key word.  Payloads are
+ * moved, never read as numbers.  `vals`/`vbuf` must be 8-byte aligned;
+ * workspace of type DFR_U64_KV64 / DFR_U32_KV64.
+ */
+int dfr_sort_u64_kv64(uint64_t* keys, uint64_t* vals, uint64_t* kbuf, uint64_t* vbuf, uint64_t n,
+                      void* ws, size_t ws_bytes, dfr_stream_t stream);
+int dfr_sort_u32_kv64(uint32_t* keys, uint64_t* vals, uint32_t* kbuf, uint64_t* vbuf, uint64_t n,
+                      void* ws, size_t ws_bytes, dfr_stream_t stream);
 
 /*
  * dfr_last_device_status -- wait for `stream`, then report the device status
@@ -193,9 +208,9 @@ int dfr_sort_u32_noalloc(uint32_t* keys, uint64_t n, dfr_stream_t stream);
 
 /* One array of a batch.  All arrays of one batch call share `key_type`. */
 typedef struct {
-    int key_type;   /* DFR_U32, DFR_U64, DFR_U64_KV or DFR_U32_KV */
+    int key_type;   /* one of enum dfr_key_type */
     void* keys;     /* [n] device, in/out */
-    void* vals;     /* [n] device payloads (kv types only, else NULL) */
+    void* vals;     /* [n] device payloads of 4 or 8 bytes (kv types only, else NULL) */
     void* kbuf;     /* [n] device scratch for keys */
     void* vbuf;     /* [n] device scratch for payloads (kv types only) */
     uint64_t n;
@@ -235,8 +250,9 @@ int dfr_sort_batch(const dfr_segment_t* segs, uint32_t count, void* ws, size_t w
  *                       of a negative value, set the sign bit of a positive one;
  *   DFR_FMT_DESCENDING  flag: largest key first; equal keys still keep input
  *                       order (stable): complement the image.
- * The width comes from the key type (DFR_U32 / DFR_U32_KV: 32-bit keys,
- * DFR_U64 / DFR_U64_KV: 64-bit keys); payloads are unchanged.  Workspace and
+ * The width comes from the key type (DFR_U32, DFR_U32_KV, DFR_U32_KV64:
+ * 32-bit keys; DFR_U64, DFR_U64_KV, DFR_U64_KV64: 64-bit keys); payloads are
+ * unchanged.  Workspace and
  * buffers as for the unsigned sorts.  DFR_ERR_INVALID_ARG for an unknown
  * format.
  */
@@ -246,7 +262,7 @@ enum dfr_key_format {
     DFR_FMT_FLOAT = 2,
     DFR_FMT_DESCENDING = 0x100
 };
-int dfr_sort_format(int key_type, int key_format, void* keys, uint32_t* vals, void* kbuf, uint32_t* vbuf,
+int dfr_sort_format(int key_type, int key_format, void* keys, void* vals, void* kbuf, void* vbuf,
                     uint64_t n, void* ws, size_t ws_bytes, dfr_stream_t stream);
 int dfr_sort_batch_format(const dfr_segment_t* segs, uint32_t count, int key_format, void* ws, size_t ws_bytes,
                           dfr_stream_t stream);
@@ -419,11 +435,12 @@ int dfr_tune_reset(void);
  * SplitMix64 generator (Steele, Lea and Flood, OOPSLA 2014) seeded with
  * `seed`: z = seed + (i+1)*0x9E3779B97F4A7C15, then the generator's mixing
  * function; u32 keys take its high 32 bits.  For the kv key types
- * vals[i] = i (the original index); `vals` is ignored otherwise.
+ * vals[i] = i (the original index, 4 or 8 bytes by the key type); `vals` is
+ * ignored otherwise.
  * Asynchronous on `stream`.  Errors: DFR_ERR_INVALID_ARG for an unknown key
  * type, n > DFR_MAX_N, or a null or misaligned pointer.
  */
-int dfr_fill_splitmix64(int key_type, void* keys, uint32_t* vals, uint64_t n, uint64_t seed,
+int dfr_fill_splitmix64(int key_type, void* keys, void* vals, uint64_t n, uint64_t seed,
                         dfr_stream_t stream);
 
 /* ---------------------------------------------------- debug and profiling -- */

@@ -48,6 +48,8 @@ def load_library(path: str):
         ("oracle_sort_u64", [p, u64]),
         ("oracle_sort_u64_kv", [p, p, u64]),
         ("oracle_sort_u32_kv", [p, p, u64]),
+        ("oracle_sort_u64_kv64", [p, p, u64]),
+        ("oracle_sort_u32_kv64", [p, p, u64]),
         ("oracle_counting_pass_u32", [p, p, u64, ctypes.c_int]),
         ("oracle_sort_format", [ctypes.c_int, ctypes.c_int, p, p, u64]),
         ("oracle_overflow_count", [p, u64, ctypes.c_int, ctypes.c_int, u64, p]),
@@ -108,18 +110,35 @@ class Oracle:
         _check(self.lib.oracle_sort_u32_kv(_ptr(k), _ptr(v), k.size))
         return k, v
 
+    def sort_u64_kv64(self, keys, vals):
+        k = np.array(keys, dtype=np.uint64, copy=True, order="C")
+        v = np.array(vals, dtype=np.uint64, copy=True, order="C")
+        if k.size != v.size:
+            raise ValueError("keys and vals differ in length")
+        _check(self.lib.oracle_sort_u64_kv64(_ptr(k), _ptr(v), k.size))
+        return k, v
+
+    def sort_u32_kv64(self, keys, vals):
+        k = np.array(keys, dtype=np.uint32, copy=True, order="C")
+        v = np.array(vals, dtype=np.uint64, copy=True, order="C")
+        if k.size != v.size:
+            raise ValueError("keys and vals differ in length")
+        _check(self.lib.oracle_sort_u32_kv64(_ptr(k), _ptr(v), k.size))
+        return k, v
+
     def sort_format(self, key_type: int, fmt: int, keys, vals=None):
         """Sort in key format `fmt` (0 unsigned, 1 signed, 2 IEEE float total
         order; | 0x100 descending).  `keys` may be any 4- or 8-byte numpy
         array; the result has the same dtype.  Returns keys, or (keys, vals)
-        for the key-value types (2: u64 + u32, 3: u32 + u32)."""
+        for the key-value types (2: u64 + u32, 3: u32 + u32, 4: u64 + u64,
+        5: u32 + u64)."""
         k = np.array(keys, copy=True, order="C")
-        width = 8 if key_type in (1, 2) else 4
+        width = 8 if key_type in (1, 2, 4) else 4
         if k.dtype.itemsize != width:
             raise ValueError("key width does not match the key type")
         v = None
-        if key_type in (2, 3):
-            v = np.array(vals, dtype=np.uint32, copy=True, order="C")
+        if key_type in (2, 3, 4, 5):
+            v = np.array(vals, dtype=np.uint64 if key_type in (4, 5) else np.uint32, copy=True, order="C")
             if v.size != k.size:
                 raise ValueError("keys and vals differ in length")
         _check(self.lib.oracle_sort_format(int(key_type), int(fmt), _ptr(k), _ptr(v) if v is not None else None,
@@ -169,6 +188,14 @@ def sort_u64_kv(keys, vals):
 
 def sort_u32_kv(keys, vals):
     return default().sort_u32_kv(keys, vals)
+
+
+def sort_u64_kv64(keys, vals):
+    return default().sort_u64_kv64(keys, vals)
+
+
+def sort_u32_kv64(keys, vals):
+    return default().sort_u32_kv64(keys, vals)
 
 
 def sort_format(key_type, fmt, keys, vals=None):

@@ -6,7 +6,7 @@
  * a fallback for it.
  *
  * What it computes: the stable ascending order of unsigned integer keys (the
- * payload, when there is one, travels with its key).  That result has a plain
+ * payload, 4 or 8 bytes when there is one, travels with its key).  That result has a plain
  * definition, so the oracle writes it out in the most direct radix form the
  * paper describes: a least-significant-digit radix sort built from counting
  * sorts (Preliminaries; Section "Least Significant Digit (LSD) Radix Sorts",
@@ -118,6 +118,49 @@ static void counting_pass_u32_kv(const uint32_t* ksrc, const uint32_t* vsrc, uin
     }
 }
 
+/* 64-bit payloads: the same deal, the payload moved as a whole 8-byte word. */
+static void counting_pass_u64_kv64(const uint64_t* ksrc, const uint64_t* vsrc, uint64_t* kdst,
+                                   uint64_t* vdst, uint64_t n, int j)
+{
+    uint64_t count[ORACLE_BUCKETS];
+    uint64_t index[ORACLE_BUCKETS];
+    uint64_t i;
+    int d;
+    const int shift = ORACLE_RADIX_BITS * j;
+
+    for (d = 0; d < ORACLE_BUCKETS; ++d) count[d] = 0;
+    for (i = 0; i < n; ++i) count[(ksrc[i] >> shift) & 255u] += 1;
+    index[0] = 0;
+    for (d = 1; d < ORACLE_BUCKETS; ++d) index[d] = index[d - 1] + count[d - 1];
+    for (i = 0; i < n; ++i) {
+        const uint64_t key = ksrc[i];
+        const uint64_t at = index[(key >> shift) & 255u]++;
+        kdst[at] = key;
+        vdst[at] = vsrc[i];
+    }
+}
+
+static void counting_pass_u32_kv64(const uint32_t* ksrc, const uint64_t* vsrc, uint32_t* kdst,
+                                   uint64_t* vdst, uint64_t n, int j)
+{
+    uint64_t count[ORACLE_BUCKETS];
+    uint64_t index[ORACLE_BUCKETS];
+    uint64_t i;
+    int d;
+    const int shift = ORACLE_RADIX_BITS * j;
+
+    for (d = 0; d < ORACLE_BUCKETS; ++d) count[d] = 0;
+    for (i = 0; i < n; ++i) count[(ksrc[i] >> shift) & 255u] += 1;
+    index[0] = 0;
+    for (d = 1; d < ORACLE_BUCKETS; ++d) index[d] = index[d - 1] + count[d - 1];
+    for (i = 0; i < n; ++i) {
+        const uint32_t key = ksrc[i];
+        const uint64_t at = index[(key >> shift) & 255u]++;
+        kdst[at] = key;
+        vdst[at] = vsrc[i];
+    }
+}
+
 int oracle_sort_u32(uint32_t* keys, uint64_t n)
 {
     uint32_t* buf;
@@ -204,6 +247,52 @@ int oracle_sort_u32_kv(uint32_t* keys, uint32_t* vals, uint64_t n)
     return 0;
 }
 
+int oracle_sort_u64_kv64(uint64_t* keys, uint64_t* vals, uint64_t n)
+{
+    uint64_t* kbuf;
+    uint64_t* vbuf;
+    uint64_t *ks = keys, *kd, *kt;
+    uint64_t *vs = vals, *vd, *vt;
+    int j;
+    if (n == 0) return 0;
+    if (keys == NULL || vals == NULL) return -2;
+    kbuf = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
+    vbuf = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
+    if (kbuf == NULL || vbuf == NULL) { free(kbuf); free(vbuf); return -1; }
+    kd = kbuf; vd = vbuf;
+    for (j = 0; j < 8; ++j) {
+        counting_pass_u64_kv64(ks, vs, kd, vd, n, j);
+        kt = ks; ks = kd; kd = kt;
+        vt = vs; vs = vd; vd = vt;
+    }
+    free(kbuf);
+    free(vbuf);
+    return 0;
+}
+
+int oracle_sort_u32_kv64(uint32_t* keys, uint64_t* vals, uint64_t n)
+{
+    uint32_t* kbuf;
+    uint64_t* vbuf;
+    uint32_t *ks = keys, *kd, *kt;
+    uint64_t *vs = vals, *vd, *vt;
+    int j;
+    if (n == 0) return 0;
+    if (keys == NULL || vals == NULL) return -2;
+    kbuf = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
+    vbuf = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
+    if (kbuf == NULL || vbuf == NULL) { free(kbuf); free(vbuf); return -1; }
+    kd = kbuf; vd = vbuf;
+    for (j = 0; j < 4; ++j) {
+        counting_pass_u32_kv64(ks, vs, kd, vd, n, j);
+        kt = ks; ks = kd; kd = kt;
+        vt = vs; vs = vd; vd = vt;
+    }
+    free(kbuf);
+    free(vbuf);
+    return 0;
+}
+
 /*
  * Key formats: the order a sort by key uses, reduced to the unsigned order of
  * a bijective image of the key's bits (written here from the definitions of
@@ -254,10 +343,11 @@ static uint64_t fmt_decode(uint64_t y, int bits, int fmt)
 }
 
 /* Sort `n` keys of key type `key_type` (0 u32, 1 u64, 2 u64 + u32 payloads,
- * 3 u32 + u32 payloads) in key format `fmt`: map every key to its image,
- * sort the images with the unsigned LSD sort above, map back.  Returns as
- * the unsigned sorts; -3 for an unknown type or format. */
-int oracle_sort_format(int key_type, int fmt, void* keys, uint32_t* vals, uint64_t n)
+ * 3 u32 + u32 payloads, 4 u64 + u64 payloads, 5 u32 + u64 payloads) in key
+ * format `fmt`: map every key to its image, sort the images with the
+ * unsigned LSD sort above, map back.  Returns as the unsigned sorts; -3 for
+ * an unknown type or format. */
+int oracle_sort_format(int key_type, int fmt, void* keys, void* vals, uint64_t n)
 {
     uint64_t i;
     int rc;
@@ -265,15 +355,19 @@ int oracle_sort_format(int key_type, int fmt, void* keys, uint32_t* vals, uint64
     if ((fmt & ~(0xFF | ORACLE_FMT_DESC)) != 0 || base > 2) return -3;
     if (n == 0) return 0;
     if (keys == NULL) return -2;
-    if (key_type == 0 || key_type == 3) {
+    if (key_type == 0 || key_type == 3 || key_type == 5) {
         uint32_t* k = (uint32_t*)keys;
         for (i = 0; i < n; ++i) k[i] = (uint32_t)fmt_encode(k[i], 32, fmt);
-        rc = key_type == 0 ? oracle_sort_u32(k, n) : oracle_sort_u32_kv(k, vals, n);
+        rc = key_type == 0   ? oracle_sort_u32(k, n)
+             : key_type == 3 ? oracle_sort_u32_kv(k, (uint32_t*)vals, n)
+                             : oracle_sort_u32_kv64(k, (uint64_t*)vals, n);
         for (i = 0; i < n; ++i) k[i] = (uint32_t)fmt_decode(k[i], 32, fmt);
-    } else if (key_type == 1 || key_type == 2) {
+    } else if (key_type == 1 || key_type == 2 || key_type == 4) {
         uint64_t* k = (uint64_t*)keys;
         for (i = 0; i < n; ++i) k[i] = fmt_encode(k[i], 64, fmt);
-        rc = key_type == 1 ? oracle_sort_u64(k, n) : oracle_sort_u64_kv(k, vals, n);
+        rc = key_type == 1   ? oracle_sort_u64(k, n)
+             : key_type == 2 ? oracle_sort_u64_kv(k, (uint32_t*)vals, n)
+                             : oracle_sort_u64_kv64(k, (uint64_t*)vals, n);
         for (i = 0; i < n; ++i) k[i] = fmt_decode(k[i], 64, fmt);
     } else {
         return -3;

@@ -41,6 +41,8 @@ DFR_U32 = 0
 DFR_U64 = 1
 DFR_U64_KV = 2
 DFR_U32_KV = 3
+DFR_U64_KV64 = 4
+DFR_U32_KV64 = 5
 
 DFR_MAX_N = (1 << 30) - 1
 DFR_NOALLOC_MAX_N = 1 << 20
@@ -59,8 +61,9 @@ DFR_SCHED_MSD = 0
 DFR_SCHED_LSD = 1
 DFR_SCHED_DFR = 2
 
-KEY_BYTES = {DFR_U32: 4, DFR_U64: 8, DFR_U64_KV: 8, DFR_U32_KV: 4}
-HAS_VALS = {DFR_U32: False, DFR_U64: False, DFR_U64_KV: True, DFR_U32_KV: True}
+KEY_BYTES = {DFR_U32: 4, DFR_U64: 8, DFR_U64_KV: 8, DFR_U32_KV: 4, DFR_U64_KV64: 8, DFR_U32_KV64: 4}
+VAL_BYTES = {DFR_U32: 0, DFR_U64: 0, DFR_U64_KV: 4, DFR_U32_KV: 4, DFR_U64_KV64: 8, DFR_U32_KV64: 8}
+HAS_VALS = {kt: vb > 0 for kt, vb in VAL_BYTES.items()}
 
 
 class DfrError(RuntimeError):
@@ -105,6 +108,8 @@ _SIGNATURES = {
     "dfr_sort_u64": (ctypes.c_int, [_vp, _vp, _u64, _vp, _sz, _vp]),
     "dfr_sort_u64_kv": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp]),
     "dfr_sort_u32_kv": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp]),
+    "dfr_sort_u64_kv64": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp]),
+    "dfr_sort_u32_kv64": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp]),
     "dfr_sort_u32_noalloc": (ctypes.c_int, [_vp, _u64, _vp]),
     "dfr_last_device_status": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_int)]),
     "dfr_get_stats": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(dfr_stats_t)]),
@@ -163,7 +168,8 @@ def load() -> ctypes.CDLL:
     return _lib
 
 
-_KEY_TYPE_NAMES = {"DFR_U32": DFR_U32, "DFR_U64": DFR_U64, "DFR_U64_KV": DFR_U64_KV, "DFR_U32_KV": DFR_U32_KV}
+_KEY_TYPE_NAMES = {"DFR_U32": DFR_U32, "DFR_U64": DFR_U64, "DFR_U64_KV": DFR_U64_KV, "DFR_U32_KV": DFR_U32_KV,
+                   "DFR_U64_KV64": DFR_U64_KV64, "DFR_U32_KV64": DFR_U32_KV64}
 
 
 def _apply_env_config(lib) -> None:
@@ -253,6 +259,16 @@ def dfr_sort_u64_kv(keys, vals, kbuf, vbuf, n, ws, ws_bytes, stream=None) -> int
 def dfr_sort_u32_kv(keys, vals, kbuf, vbuf, n, ws, ws_bytes, stream=None) -> int:
     return load().dfr_sort_u32_kv(_ptr(keys), _ptr(vals), _ptr(kbuf), _ptr(vbuf), int(n), _ptr(ws),
                                   int(ws_bytes), _stream(stream))
+
+
+def dfr_sort_u64_kv64(keys, vals, kbuf, vbuf, n, ws, ws_bytes, stream=None) -> int:
+    return load().dfr_sort_u64_kv64(_ptr(keys), _ptr(vals), _ptr(kbuf), _ptr(vbuf), int(n), _ptr(ws),
+                                    int(ws_bytes), _stream(stream))
+
+
+def dfr_sort_u32_kv64(keys, vals, kbuf, vbuf, n, ws, ws_bytes, stream=None) -> int:
+    return load().dfr_sort_u32_kv64(_ptr(keys), _ptr(vals), _ptr(kbuf), _ptr(vbuf), int(n), _ptr(ws),
+                                    int(ws_bytes), _stream(stream))
 
 
 def dfr_sort_u32_noalloc(keys, n, stream=None) -> int:
@@ -462,7 +478,8 @@ class Sorter:
         kb = KEY_BYTES[key_type]
         kdt = torch.int32 if kb == 4 else torch.int64
         self.kbuf = torch.empty(max(1, self.capacity), dtype=kdt, device=self.device)
-        self.vbuf = (torch.empty(max(1, self.capacity), dtype=torch.int32, device=self.device)
+        vdt = torch.int64 if VAL_BYTES[key_type] == 8 else torch.int32
+        self.vbuf = (torch.empty(max(1, self.capacity), dtype=vdt, device=self.device)
                      if HAS_VALS[key_type] else None)
         self.ws_bytes = dfr_workspace_bytes(key_type, max(2, self.capacity))
         # zeroed once so the status word reads DFR_OK before the first call
@@ -494,7 +511,7 @@ class Sorter:
         kt = self.key_type
         self._arg(keys, "keys", n, KEY_BYTES[kt])
         if HAS_VALS[kt]:
-            self._arg(vals, "vals", n, 4)
+            self._arg(vals, "vals", n, VAL_BYTES[kt])
         elif vals is not None:
             raise ValueError("payloads given to a key-only sorter")
         if key_format != DFR_FMT_UNSIGNED:
@@ -505,8 +522,12 @@ class Sorter:
             rc = dfr_sort_u64(keys, self.kbuf, n, self.ws, self.ws_bytes, stream)
         elif kt == DFR_U64_KV:
             rc = dfr_sort_u64_kv(keys, vals, self.kbuf, self.vbuf, n, self.ws, self.ws_bytes, stream)
-        else:
+        elif kt == DFR_U32_KV:
             rc = dfr_sort_u32_kv(keys, vals, self.kbuf, self.vbuf, n, self.ws, self.ws_bytes, stream)
+        elif kt == DFR_U64_KV64:
+            rc = dfr_sort_u64_kv64(keys, vals, self.kbuf, self.vbuf, n, self.ws, self.ws_bytes, stream)
+        else:
+            rc = dfr_sort_u32_kv64(keys, vals, self.kbuf, self.vbuf, n, self.ws, self.ws_bytes, stream)
         check(rc, "sort")
         return rc
 

@@ -33,7 +33,7 @@ std::mutex g_grid_mu;
 std::map<std::pair<const void*, int>, int> g_grid_cache;
 
 // The tuning table: built-in entries written by the autotuner, overridable.
-constexpr int kKeyTypes = 4;
+constexpr int kKeyTypes = 6;
 const dfr_tune_t kBuiltinTune[kKeyTypes][DFR_TUNE_CLASSES] = {
 #include "dfr_tune_table.inc"
 };
@@ -130,6 +130,8 @@ int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, 
   switch (key_type) {
     case DFR_U32: return run_u32(a, n, batch, ws, wsb, st, fmt);
     case DFR_U32_KV: return run_u32_kv(a, n, batch, ws, wsb, st, fmt);
+    case DFR_U64_KV64: return run_u64_kv64(a, n, batch, ws, wsb, st, fmt);
+    case DFR_U32_KV64: return run_u32_kv64(a, n, batch, ws, wsb, st, fmt);
     case DFR_U64: return run_u64(a, n, batch, ws, wsb, st, fmt);
     case DFR_U64_KV: return run_u64_kv(a, n, batch, ws, wsb, st, fmt);
     default: return DFR_ERR_INVALID_ARG;
@@ -141,6 +143,8 @@ int graph_typed(int key_type, const HostArr* a, uint32_t n, void* ws, size_t wsb
   switch (key_type) {
     case DFR_U32: return graph_u32(a, n, ws, wsb, out, nodes);
     case DFR_U32_KV: return graph_u32_kv(a, n, ws, wsb, out, nodes);
+    case DFR_U64_KV64: return graph_u64_kv64(a, n, ws, wsb, out, nodes);
+    case DFR_U32_KV64: return graph_u32_kv64(a, n, ws, wsb, out, nodes);
     case DFR_U64: return graph_u64(a, n, ws, wsb, out, nodes);
     case DFR_U64_KV: return graph_u64_kv(a, n, ws, wsb, out, nodes);
     default: return DFR_ERR_INVALID_ARG;
@@ -151,6 +155,8 @@ int ws_typed(int key_type, uint64_t ntot, uint32_t narr, size_t* bytes) {
   switch (key_type) {
     case DFR_U32: *bytes = ws_u32(ntot, narr); return DFR_OK;
     case DFR_U32_KV: *bytes = ws_u32_kv(ntot, narr); return DFR_OK;
+    case DFR_U64_KV64: *bytes = ws_u64_kv64(ntot, narr); return DFR_OK;
+    case DFR_U32_KV64: *bytes = ws_u32_kv64(ntot, narr); return DFR_OK;
     case DFR_U64: *bytes = ws_u64(ntot, narr); return DFR_OK;
     case DFR_U64_KV: *bytes = ws_u64_kv(ntot, narr); return DFR_OK;
     default: return DFR_ERR_INVALID_ARG;
@@ -167,6 +173,8 @@ uint64_t dfr_lsd_min_keys(int key_type) {
   switch (key_type) {
     case DFR_U32: return lsd_min_n<uint32_t, NoVal>();
     case DFR_U32_KV: return lsd_min_n<uint32_t, uint32_t>();
+    case DFR_U64_KV64: return lsd_min_n<uint64_t, uint64_t>();
+    case DFR_U32_KV64: return lsd_min_n<uint32_t, uint64_t>();
     case DFR_U64: return lsd_min_n<uint64_t, NoVal>();
     case DFR_U64_KV: return lsd_min_n<uint64_t, uint32_t>();
     default: return 0;
@@ -198,6 +206,18 @@ int dfr_sort_u32_kv(uint32_t* keys, uint32_t* vals, uint32_t* kbuf, uint32_t* vb
                     size_t ws_bytes, dfr_stream_t stream) {
   const HostArr a{keys, kbuf, vals, vbuf, n};
   return run_u32_kv(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED);
+}
+
+int dfr_sort_u64_kv64(uint64_t* keys, uint64_t* vals, uint64_t* kbuf, uint64_t* vbuf, uint64_t n, void* ws,
+                      size_t ws_bytes, dfr_stream_t stream) {
+  const HostArr a{keys, kbuf, vals, vbuf, n};
+  return run_u64_kv64(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED);
+}
+
+int dfr_sort_u32_kv64(uint32_t* keys, uint64_t* vals, uint32_t* kbuf, uint64_t* vbuf, uint64_t n, void* ws,
+                      size_t ws_bytes, dfr_stream_t stream) {
+  const HostArr a{keys, kbuf, vals, vbuf, n};
+  return run_u32_kv64(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED);
 }
 
 int dfr_last_device_status(const void* ws, dfr_stream_t stream, int* status) {
@@ -362,7 +382,7 @@ int dfr_tune_reset(void) {
   return DFR_OK;
 }
 
-int dfr_sort_format(int key_type, int key_format, void* keys, uint32_t* vals, void* kbuf, uint32_t* vbuf,
+int dfr_sort_format(int key_type, int key_format, void* keys, void* vals, void* kbuf, void* vbuf,
                     uint64_t n, void* ws, size_t ws_bytes, dfr_stream_t stream) {
   const HostArr a{keys, kbuf, vals, vbuf, n};
   return run_typed(key_type, &a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, key_format);

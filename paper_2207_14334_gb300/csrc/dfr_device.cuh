@@ -60,6 +60,17 @@ constexpr int EXTRA_LEVELS = 2;  // levels launched beyond key bits / RB (room f
 constexpr uint32_t T_WARP = 32;  // tiny-bucket threshold (warp sort)
 
 struct NoVal {};
+
+// The payload type of a sort: V itself (uint32_t or uint64_t), and a
+// placeholder for key-only sorts.
+template <class V>
+struct ValT {
+  using type = V;
+};
+template <>
+struct ValT<NoVal> {
+  using type = uint32_t;
+};
 // u32 key-only sorts have two CTA sorts: k_ctasort32 for buckets whose keys
 // vary in at most CTA32_SPAN bits (the usual case), the general k_ctasort
 // (second queue) for the rest; the classifiers route by a bound on the span.
@@ -227,7 +238,7 @@ struct Ctx {
   LsdCtl* lsd;
   uint32_t* lsd_st[2];    // look-back words of the two passes ([tiles][M]; pass 0 only for key-value)
   void* pool_k;           // mode 2: overflow regions, M x est_ocap keys
-  uint32_t* pool_v;       //          and payloads
+  void* pool_v;           //          and payloads
 };
 
 // ------------------------------------------------------------------ helpers
@@ -501,14 +512,14 @@ __device__ __forceinline__ void block_or2(K& a, K& b, K* sh) {
 
 // Stable sort of len <= 32 records by one warp (insertion-sort semantics:
 // rank = keys below + equal keys earlier).  src and dst may alias.
-template <class K, bool KV>
-__device__ __forceinline__ void warp_sort_tiny(const K* src, const uint32_t* vsrc, K* dst,
-                                               uint32_t* vdst, uint32_t off, uint32_t len) {
+template <class K, bool KV, class VT = uint32_t>
+__device__ __forceinline__ void warp_sort_tiny(const K* src, const VT* vsrc, K* dst, VT* vdst, uint32_t off,
+                                               uint32_t len) {
   const uint32_t lane = lane_id();
   const bool valid = lane < len;
   const K k = valid ? src[off + lane] : K(0);
-  uint32_t v = 0;
-  if constexpr (KV) v = valid ? vsrc[off + lane] : 0u;
+  VT v = 0;
+  if constexpr (KV) v = valid ? vsrc[off + lane] : VT(0);
   uint32_t rank = 0;
   for (uint32_t j = 0; j < len; ++j) {
     const K kj = __shfl_sync(FULL, k, (int)j);
@@ -805,8 +816,9 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
     }
     if (n <= T_WARP) {
       if (threadIdx.x < 32) {
-        warp_sort_tiny<K, KV>(reinterpret_cast<const K*>(ad.keys), reinterpret_cast<const uint32_t*>(ad.vals),
-                              reinterpret_cast<K*>(ad.keys), reinterpret_cast<uint32_t*>(ad.vals), 0u, n);
+        using VT = typename ValT<V>::type;
+        warp_sort_tiny<K, KV, VT>(reinterpret_cast<const K*>(ad.keys), reinterpret_cast<const VT*>(ad.vals),
+                                  reinterpret_cast<K*>(ad.keys), reinterpret_cast<VT*>(ad.vals), 0u, n);
         if (threadIdx.x == 0) {
           atomicAdd(&ctl->tiny_buckets, 1ull);
           atomicAdd(&ctl->tiny_keys, (unsigned long long)n);
@@ -951,7 +963,8 @@ constexpr size_t scatter_smem_bytes() {
   constexpr size_t TILE = (size_t)NT * KPT;
   // staging area; counters (per warp for the stable key-value ranking, one
   // block-wide set otherwise); tile digit starts; global offsets
-  return TILE * sizeof(K) + (KV ? TILE * 4 : 0) + (KV ? (size_t)(NT / 32) * M * 4 : (size_t)M * 4) + 2 * M * 4;
+  return TILE * sizeof(K) + (KV ? TILE * sizeof(typename ValT<V>::type) : 0) +
+         (KV ? (size_t)(NT / 32) * M * 4 : (size_t)M * 4) + 2 * M * 4;
 }
 
 // CTAs per SM the scatter-shaped kernels are compiled for: key-only tiles of
@@ -1151,8 +1164,9 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false>())) k_s
   static_assert(KV || KPT % VK == 0, "vector loads cover whole items");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   K* s_keys = reinterpret_cast<K*>(smem_raw);
-  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + TILE);
-  uint32_t* s_cnt = s_vals + (KV ? TILE : 0);  // KV: [NW][M] per warp; else [M]
+  using VT = typename ValT<V>::type;
+  VT* s_vals = reinterpret_cast<VT*>(s_keys + TILE);
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_vals + (KV ? TILE : 0));  // KV: [NW][M] per warp; else [M]
   uint32_t* s_tstart = s_cnt + (KV ? NW * M : M);
   uint32_t* s_goff = s_tstart + M;  // global destination of staged element e of digit d = s_goff[d] + e
   __shared__ uint32_t s_scan[16];
@@ -1192,8 +1206,8 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false>())) k_s
     const ArrDesc ad = c.arrs[seg.arr];
     const K* src = reinterpret_cast<const K*>(seg.parity ? ad.buf : ad.keys);
     K* dst = reinterpret_cast<K*>(seg.parity ? ad.keys : ad.buf);
-    const uint32_t* vsrc = reinterpret_cast<const uint32_t*>(seg.parity ? ad.vbuf : ad.vals);
-    uint32_t* vdst = reinterpret_cast<uint32_t*>(seg.parity ? ad.vals : ad.vbuf);
+    const VT* vsrc = reinterpret_cast<const VT*>(seg.parity ? ad.vbuf : ad.vals);
+    VT* vdst = reinterpret_cast<VT*>(seg.parity ? ad.vals : ad.vbuf);
     const uint32_t j = t - seg.tile_start;
     const uint32_t tb = tile_base<K>(seg.off) + j * TILE;         // first element of the tile
     const uint32_t seg_end = seg.off + seg.len;
@@ -1204,7 +1218,7 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false>())) k_s
 
     K k[KPT];
     uint32_t r[KPT];
-    uint32_t v[KV ? KPT : 1];
+    VT v[KV ? KPT : 1];
     if constexpr (KV) {
       // warp-striped: item i of lane l is element wb + i*32 + l
       const uint32_t wb = warp * 32u * KPT;
@@ -1595,17 +1609,18 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
       const ArrDesc ad = c.arrs[seg.arr];
       const uint32_t pout = seg.parity ^ 1u;
       const K* psrc = reinterpret_cast<const K*>(pout ? ad.buf : ad.keys);
-      const uint32_t* pvsrc = reinterpret_cast<const uint32_t*>(pout ? ad.vbuf : ad.vals);
+      using VT = typename ValT<V>::type;
+      const VT* pvsrc = reinterpret_cast<const VT*>(pout ? ad.vbuf : ad.vals);
       for (uint32_t i = warp; i < tn; i += 8) {
         const uint32_t o = s_tiny_off[i];
         const uint32_t len = s_tiny_len[i] & 0x7fffffffu;
         if (s_tiny_len[i] & 0x80000000u) {
           if (lane < len) {
             reinterpret_cast<K*>(ad.keys)[o + lane] = psrc[o + lane];
-            if constexpr (KV) reinterpret_cast<uint32_t*>(ad.vals)[o + lane] = pvsrc[o + lane];
+            if constexpr (KV) reinterpret_cast<VT*>(ad.vals)[o + lane] = pvsrc[o + lane];
           }
         } else {
-          warp_sort_tiny<K, KV>(psrc, pvsrc, reinterpret_cast<K*>(ad.keys), reinterpret_cast<uint32_t*>(ad.vals),
+          warp_sort_tiny<K, KV, VT>(psrc, pvsrc, reinterpret_cast<K*>(ad.keys), reinterpret_cast<VT*>(ad.vals),
                                 o, len);
         }
       }
@@ -1658,7 +1673,8 @@ constexpr size_t ctasort_smem_bytes() {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr size_t CAPX = (size_t)NT * KPT + 16 / sizeof(K);
   // key-value sorts add u16 staged positions and a u16 output permutation
-  return CAPX * sizeof(K) * (KV ? 1 : 2) + (KV ? (size_t)NT * KPT * (4 + 2 + 2) : 0) + (size_t)(NT / 32) * M * 4 +
+  return CAPX * sizeof(K) * (KV ? 1 : 2) + (KV ? (size_t)NT * KPT * (sizeof(typename ValT<V>::type) + 2 + 2) : 0) +
+         (size_t)(NT / 32) * M * 4 +
          M * 4;
 }
 
@@ -1684,8 +1700,9 @@ __device__ __forceinline__ uint32_t granule_shift(const K* g) {
 }
 
 template <class K, class V, int NT, int KPT, int KPTA>
-__device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const uint32_t* vsrc, K* dst, uint32_t* vdst,
-                                                uint32_t off, uint32_t len, bool par, K* s_keys, uint32_t* s_vals,
+__device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const typename ValT<V>::type* vsrc, K* dst,
+                                                typename ValT<V>::type* vdst, uint32_t off, uint32_t len, bool par,
+                                                K* s_keys, typename ValT<V>::type* s_vals,
                                                 uint32_t* s_whist, uint32_t* s_dstart, uint32_t* s_scan,
                                                 uint32_t* s_scan16, uint32_t* s_maxc, uint32_t* s_mixed,
                                                 unsigned long long* s_orv, K* s_out, uint16_t* s_pos,
@@ -1701,7 +1718,7 @@ __device__ __forceinline__ void cta_sort_bucket(Ctl* ctl, const K* src, const ui
   const uint32_t wvalid = len > wb ? min(len - wb, 32u * KPTA) : 0u;
   K k[KPTA];
   uint32_t r[KPTA];
-  uint32_t v[KV ? KPTA : 1];
+  typename ValT<V>::type v[KV ? KPTA : 1];
   K orv = 0, nandv = 0;
 #pragma unroll
   for (int i = 0; i < KPTA; ++i) {
@@ -2004,8 +2021,9 @@ __global__ void __launch_bounds__(NT, (ctasort_min_blocks<K, V, NT>())) k_ctasor
   extern __shared__ __align__(16) unsigned char smem_raw[];
   K* s_keys = reinterpret_cast<K*>(smem_raw);
   K* s_out = s_keys + CAPX;  // key-only sorts only
-  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + (KV ? CAPX : 2 * CAPX));
-  uint32_t* s_whist = s_vals + (KV ? CAP : 0);
+  using VT = typename ValT<V>::type;
+  VT* s_vals = reinterpret_cast<VT*>(s_keys + (KV ? CAPX : 2 * CAPX));
+  uint32_t* s_whist = reinterpret_cast<uint32_t*>(s_vals + (KV ? CAP : 0));
   uint32_t* s_dstart = s_whist + NW * M;
   uint16_t* s_pos = reinterpret_cast<uint16_t*>(s_dstart + M);  // key-value sorts only
   uint16_t* s_perm = s_pos + (KV ? CAP : 0);
@@ -2032,9 +2050,9 @@ __global__ void __launch_bounds__(NT, (ctasort_min_blocks<K, V, NT>())) k_ctasor
     const ArrDesc ad = c.arrs[it.arr];
     const bool par = (it.info & ITEM_PARITY) != 0u;
     const K* src = reinterpret_cast<const K*>(par ? ad.buf : ad.keys);
-    const uint32_t* vsrc = reinterpret_cast<const uint32_t*>(par ? ad.vbuf : ad.vals);
+    const VT* vsrc = reinterpret_cast<const VT*>(par ? ad.vbuf : ad.vals);
     K* dst = reinterpret_cast<K*>(ad.keys);
-    uint32_t* vdst = reinterpret_cast<uint32_t*>(ad.vals);
+    VT* vdst = reinterpret_cast<VT*>(ad.vals);
     const uint32_t off = it.off, len = min(it.len, CAP);
     if (it.info & ITEM_COPY) {
       for (uint32_t e = threadIdx.x; e < len; e += NT) {
@@ -2089,7 +2107,7 @@ template <class K, class V, int WKPT>
 constexpr size_t warpsort_warp_bytes() {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr size_t WCAP = (size_t)32 * WKPT;
-  return WCAP * sizeof(K) + (KV ? WCAP * 4 : 0) + M * 4;
+  return WCAP * sizeof(K) + (KV ? WCAP * sizeof(typename ValT<V>::type) : 0) + M * 4;
 }
 
 // Diversion sort of small buckets (T_WARP < len <= 32 * WKPT): every warp
@@ -2106,9 +2124,10 @@ __global__ void __launch_bounds__(WPB * 32) k_warpsort(Ctx c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   unsigned char* base = smem_raw + (size_t)warp * warpsort_warp_bytes<K, V, WKPT>();
+  using VT = typename ValT<V>::type;
   K* sk = reinterpret_cast<K*>(base);
-  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + WCAP);
-  uint32_t* wh = sv + (KV ? WCAP : 0);
+  VT* sv = reinterpret_cast<VT*>(sk + WCAP);
+  uint32_t* wh = reinterpret_cast<uint32_t*>(sv + (KV ? WCAP : 0));
   Ctl* ctl = c.ctl;
   const uint32_t count = min(ctl->wq_count, c.wqcap);
   for (;;) {
@@ -2120,14 +2139,14 @@ __global__ void __launch_bounds__(WPB * 32) k_warpsort(Ctx c) {
     const ArrDesc ad = c.arrs[it.arr];
     const bool par = (it.info & ITEM_PARITY) != 0u;
     const K* src = reinterpret_cast<const K*>(par ? ad.buf : ad.keys);
-    const uint32_t* vsrc = reinterpret_cast<const uint32_t*>(par ? ad.vbuf : ad.vals);
+    const VT* vsrc = reinterpret_cast<const VT*>(par ? ad.vbuf : ad.vals);
     K* dst = reinterpret_cast<K*>(ad.keys);
-    uint32_t* vdst = reinterpret_cast<uint32_t*>(ad.vals);
+    VT* vdst = reinterpret_cast<VT*>(ad.vals);
     const uint32_t off = it.off, len = min(it.len, WCAP);
     const uint32_t kpt = (len + 31u) / 32u;
     K k[WKPT];
     uint32_t r[WKPT];
-    uint32_t v[KV ? WKPT : 1];
+    VT v[KV ? WKPT : 1];
     K orv = 0, nandv = 0;
 #pragma unroll
     for (int i = 0; i < WKPT; ++i) {
@@ -2290,7 +2309,10 @@ __global__ void __launch_bounds__(NT) k_copy(Ctx c) {
     const K val = (K)it.value;
     for (uint32_t i = b + threadIdx.x; i < e; i += NT) {
       dst[i] = val;
-      if constexpr (KV) reinterpret_cast<uint32_t*>(ad.vals)[i] = reinterpret_cast<const uint32_t*>(ad.vbuf)[i];
+      if constexpr (KV) {
+        using VT = typename ValT<V>::type;
+        reinterpret_cast<VT*>(ad.vals)[i] = reinterpret_cast<const VT*>(ad.vbuf)[i];
+      }
     }
     __syncthreads();
   }

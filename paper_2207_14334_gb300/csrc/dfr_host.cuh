@@ -42,6 +42,14 @@ dfr_tune_t rt_tune(int key_type, uint64_t mean_keys);
 enum ProfKind { PK_INIT = 0, PK_ROOT_COUNT, PK_ROOT_CLASSIFY, PK_LEVEL_COUNT, PK_SCATTER, PK_CLASSIFY, PK_CTASORT,
                 PK_COPY, PK_H2D, PK_WARPSORT, PK_KEYFMT, PK_LSD_PASS, PK_LSD_PLAN };
 
+// Properties of the key types of the C interface (enum dfr_key_type).
+inline bool key_type_valid(int kt) { return kt >= DFR_U32 && kt <= DFR_U32_KV64; }
+inline size_t key_bytes_of(int kt) { return (kt == DFR_U64 || kt == DFR_U64_KV || kt == DFR_U64_KV64) ? 8u : 4u; }
+inline size_t val_bytes_of(int kt) {  // 0 for key-only types
+  return (kt == DFR_U64_KV || kt == DFR_U32_KV) ? 4u : (kt == DFR_U64_KV64 || kt == DFR_U32_KV64) ? 8u : 0u;
+}
+inline bool has_vals(int kt) { return val_bytes_of(kt) != 0u; }
+
 inline bool fmt_valid(int fmt) {
   return (fmt & ~(0xFF | DFR_FMT_DESCENDING)) == 0 && (fmt & 0xFF) <= DFR_FMT_FLOAT;
 }
@@ -76,6 +84,16 @@ struct Cfg<uint64_t, NoVal> {
 };
 template <>
 struct Cfg<uint64_t, uint32_t> {
+  static constexpr int SNT = 512, SKPT = 8, CNT = 512, CKPT = 8, WPB = 8, WKPT = 16;
+};
+// 64-bit payloads: the same tiles and capacities (16-byte records for u64
+// keys: the CTA sort's staging grows to 4096 x (8 + 8 + 2 + 2) bytes)
+template <>
+struct Cfg<uint64_t, uint64_t> {
+  static constexpr int SNT = 512, SKPT = 8, CNT = 512, CKPT = 8, WPB = 8, WKPT = 16;
+};
+template <>
+struct Cfg<uint32_t, uint64_t> {
   static constexpr int SNT = 512, SKPT = 8, CNT = 512, CKPT = 8, WPB = 8, WKPT = 16;
 };
 template <class K, class V>
@@ -190,7 +208,7 @@ Layout make_layout(uint64_t ntot, uint32_t narr) {
     l.pool_k = o;
     o = align256(o + (size_t)M * l.est_ocap * sizeof(K));
     l.pool_v = o;
-    o = align256(o + (KV ? (size_t)M * l.est_ocap * 4 : 0));
+    o = align256(o + (KV ? (size_t)M * l.est_ocap * sizeof(typename ValT<V>::type) : 0));
   }
   l.total = o;
   return l;
@@ -227,7 +245,7 @@ inline Ctx make_ctx(void* ws, const Layout& l, uint32_t narr) {
     c.lsd_st[0] = reinterpret_cast<uint32_t*>(b + l.lsd_st0);
     c.lsd_st[1] = reinterpret_cast<uint32_t*>(b + l.lsd_st1);
     c.pool_k = b + l.pool_k;
-    c.pool_v = reinterpret_cast<uint32_t*>(b + l.pool_v);
+    c.pool_v = b + l.pool_v;
     c.lsd_tiles_a = l.lsd_tiles_a;
     c.lsd_tiles_b_cap = l.lsd_tiles_b_cap;
     c.est_cap = l.est_cap;
@@ -244,6 +262,7 @@ inline bool ranges_overlap(const void* a, uint64_t abytes, const void* b, uint64
 template <class K, class V>
 int check_arrays(const HostArr* arrs, uint32_t narr, uint64_t* ntot_out) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
+  constexpr uint64_t VB = sizeof(typename ValT<V>::type);  // payload bytes
   uint64_t ntot = 0;
   for (uint32_t a = 0; a < narr; ++a) {
     const HostArr& h = arrs[a];
@@ -253,14 +272,14 @@ int check_arrays(const HostArr* arrs, uint32_t narr, uint64_t* ntot_out) {
     if (KV && (!h.vals || !h.vbuf)) return DFR_ERR_INVALID_ARG;
     // element alignment (the 16-byte vector body of every load starts from it)
     if (((uintptr_t)h.keys % sizeof(K)) || ((uintptr_t)h.buf % sizeof(K))) return DFR_ERR_INVALID_ARG;
-    if (KV && (((uintptr_t)h.vals % 4) || ((uintptr_t)h.vbuf % 4))) return DFR_ERR_INVALID_ARG;
+    if (KV && (((uintptr_t)h.vals % VB) || ((uintptr_t)h.vbuf % VB))) return DFR_ERR_INVALID_ARG;
     if (ranges_overlap(h.keys, h.n * sizeof(K), h.buf, h.n * sizeof(K))) return DFR_ERR_INVALID_ARG;
     if (KV) {
-      if (ranges_overlap(h.vals, h.n * 4, h.vbuf, h.n * 4)) return DFR_ERR_INVALID_ARG;
-      if (ranges_overlap(h.vals, h.n * 4, h.keys, h.n * sizeof(K))) return DFR_ERR_INVALID_ARG;
-      if (ranges_overlap(h.vals, h.n * 4, h.buf, h.n * sizeof(K))) return DFR_ERR_INVALID_ARG;
-      if (ranges_overlap(h.vbuf, h.n * 4, h.keys, h.n * sizeof(K))) return DFR_ERR_INVALID_ARG;
-      if (ranges_overlap(h.vbuf, h.n * 4, h.buf, h.n * sizeof(K))) return DFR_ERR_INVALID_ARG;
+      if (ranges_overlap(h.vals, h.n * VB, h.vbuf, h.n * VB)) return DFR_ERR_INVALID_ARG;
+      if (ranges_overlap(h.vals, h.n * VB, h.keys, h.n * sizeof(K))) return DFR_ERR_INVALID_ARG;
+      if (ranges_overlap(h.vals, h.n * VB, h.buf, h.n * sizeof(K))) return DFR_ERR_INVALID_ARG;
+      if (ranges_overlap(h.vbuf, h.n * VB, h.keys, h.n * sizeof(K))) return DFR_ERR_INVALID_ARG;
+      if (ranges_overlap(h.vbuf, h.n * VB, h.buf, h.n * sizeof(K))) return DFR_ERR_INVALID_ARG;
     }
     ntot += h.n;
   }
@@ -307,8 +326,9 @@ void ctx_plan(Ctx* c, const dfr_tune_t& t) {
 
 template <class K, class V>
 constexpr int key_type_of() {
-  return std::is_same<V, NoVal>::value ? (sizeof(K) == 8 ? DFR_U64 : DFR_U32)
-                                       : (sizeof(K) == 8 ? DFR_U64_KV : DFR_U32_KV);
+  return std::is_same<V, NoVal>::value     ? (sizeof(K) == 8 ? DFR_U64 : DFR_U32)
+         : std::is_same<V, uint32_t>::value ? (sizeof(K) == 8 ? DFR_U64_KV : DFR_U32_KV)
+                                            : (sizeof(K) == 8 ? DFR_U64_KV64 : DFR_U32_KV64);
 }
 
 template <class K, class V, int G = 0>
@@ -596,14 +616,20 @@ int run_u32(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cuda
 int run_u32_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
 int run_u64(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
 int run_u64_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
+int run_u64_kv64(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
+int run_u32_kv64(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
 size_t ws_u32(uint64_t ntot, uint32_t narr);
 size_t ws_u32_kv(uint64_t ntot, uint32_t narr);
 size_t ws_u64(uint64_t ntot, uint32_t narr);
 size_t ws_u64_kv(uint64_t ntot, uint32_t narr);
+size_t ws_u64_kv64(uint64_t ntot, uint32_t narr);
+size_t ws_u32_kv64(uint64_t ntot, uint32_t narr);
 int graph_u32(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes);
 int graph_u32_kv(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes);
 int graph_u64(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes);
 int graph_u64_kv(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes);
+int graph_u64_kv64(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes);
+int graph_u32_kv64(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes);
 // Dispatch by key type, and the device error word as a DFR status (dfr_api.cu).
 int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st,
               int fmt = DFR_FMT_UNSIGNED);

@@ -54,7 +54,8 @@ constexpr size_t lsd_smem_bytes() {
   // staging area; counters (per warp for key-value, block-wide otherwise);
   // per digit: tile start, main destination base, main-part length, overflow
   // base, and the estimated pass's D0 counts
-  return TILE * sizeof(K) + (KV ? TILE * 4 : 0) + (KV ? (size_t)(NT / 32) * M * 4 : (size_t)M * 4) + 5 * M * 4;
+  return TILE * sizeof(K) + (KV ? TILE * sizeof(typename ValT<V>::type) : 0) +
+         (KV ? (size_t)(NT / 32) * M * 4 : (size_t)M * 4) + 5 * M * 4;
 }
 
 // One LSD pass (pass 0 deals D1 into buf / the overflow regions, pass 1 deals
@@ -72,8 +73,9 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, EST>())) k_lsd
   static_assert(KV || KPT % VK == 0, "vector loads cover whole items");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   K* s_keys = reinterpret_cast<K*>(smem_raw);
-  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + TILE);
-  uint32_t* s_cnt = s_vals + (KV ? TILE : 0);  // KV: [NW][M] per warp; else [M]
+  using VT = typename ValT<V>::type;
+  VT* s_vals = reinterpret_cast<VT*>(s_keys + TILE);
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_vals + (KV ? TILE : 0));  // KV: [NW][M] per warp; else [M]
   uint32_t* s_tstart = s_cnt + (KV ? NW * M : M);
   uint32_t* s_dst = s_tstart + M;  // main destination of staged element e of digit d: s_dst[d] + e
   uint32_t* s_lim = s_dst + M;     // staged elements [tstart, tstart + lim) of digit d go to the main bucket
@@ -128,18 +130,18 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, EST>())) k_lsd
     if (t >= ntiles) break;
 
     const K* src;
-    const uint32_t* vsrc;
+    const VT* vsrc;
     uint32_t tb, vlo, vhi;
     if constexpr (PASS == 0) {
       src = reinterpret_cast<const K*>(ad.keys);
-      vsrc = reinterpret_cast<const uint32_t*>(ad.vals);
+      vsrc = reinterpret_cast<const VT*>(ad.vals);
       tb = t * TILE;
       vlo = 0u;
       vhi = min(TILE, ad.n - tb);
     } else {
       const uint32_t p = s_p;
       src = reinterpret_cast<const K*>((p & 1u) ? c.pool_k : ad.buf);
-      vsrc = reinterpret_cast<const uint32_t*>((p & 1u) ? (void*)c.pool_v : ad.vbuf);
+      vsrc = reinterpret_cast<const VT*>((p & 1u) ? (void*)c.pool_v : ad.vbuf);
       const uint32_t poff = lsd->poff[p], plen = lsd->plen[p];
       tb = tile_base<K>(poff) + (t - lsd->pstart[p]) * TILE;
       vlo = poff > tb ? poff - tb : 0u;
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, EST>())) k_lsd
 
     K k[KPT];
     uint32_t r[KPT];
-    uint32_t v[KV ? KPT : 1];
+    VT v[KV ? KPT : 1];
     if constexpr (KV) {
       // warp-striped: item i of lane l is element wb + i*32 + l
       const uint32_t wb = warp * 32u * KPT;
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, EST>())) k_lsd
     // Coalesced write-out of the staged runs.
     if (s_fail == 0u) {
       K* dk = reinterpret_cast<K*>(pass == 0 ? ad.buf : ad.keys);
-      uint32_t* dv = reinterpret_cast<uint32_t*>(pass == 0 ? ad.vbuf : ad.vals);
+      VT* dv = reinterpret_cast<VT*>(pass == 0 ? ad.vbuf : ad.vals);
       K* pk = reinterpret_cast<K*>(c.pool_k);
 #pragma unroll 4
       for (uint32_t e = threadIdx.x; e < nvalid; e += NT) {
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, EST>())) k_lsd
           const uint32_t q = s_ovf[d] + e;
           if (q < pool_n) {
             pk[q] = kk;
-            if constexpr (KV) c.pool_v[q] = s_vals[e];
+            if constexpr (KV) reinterpret_cast<VT*>(c.pool_v)[q] = s_vals[e];
           } else {
             record_error(c.ctl, DERR_BOUNDS, ERR_SITE_LSD_WRITE);
           }

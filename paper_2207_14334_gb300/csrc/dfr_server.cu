@@ -95,14 +95,12 @@ struct Request {
 constexpr size_t kMaxBatch = 4096;  // default cap on requests per batched launch sequence
 constexpr int kStatusSlot = 64;     // bytes of pinned memory per batch for its error word
 
-size_t key_bytes_of(int kt) { return (kt == DFR_U64 || kt == DFR_U64_KV) ? 8u : 4u; }
-bool has_vals(int kt) { return kt == DFR_U64_KV || kt == DFR_U32_KV; }
 
 // Scratch bytes the server provides for a request without its own buffers.
 size_t scratch_bytes(const dfr_segment_t& s) {
   size_t b = 0;
   if (!s.kbuf) b += align256(s.n * key_bytes_of(s.key_type));
-  if (has_vals(s.key_type) && !s.vbuf) b += align256(s.n * sizeof(uint32_t));
+  if (has_vals(s.key_type) && !s.vbuf) b += align256(s.n * val_bytes_of(s.key_type));
   return b;
 }
 
@@ -215,7 +213,7 @@ dfr_server::Batch* dfr_server::form_batch(std::vector<dfr_segment_t>* segs) {
     }
     if (has_vals(kt) && !g.vbuf) {
       g.vbuf = base + at;
-      at += align256(g.n * sizeof(uint32_t));
+      at += align256(g.n * val_bytes_of(kt));
     }
     segs->push_back(g);
   }
@@ -365,12 +363,12 @@ int dfr_server_create(dfr_server_t** out, int device, size_t mem_budget_bytes, i
 int dfr_submit_after(dfr_server_t* s, const dfr_segment_t* req, void* ready_event, uint64_t* ticket) {
   if (!s || !req || !ticket) return DFR_ERR_INVALID_ARG;
   const dfr_segment_t& g = *req;
-  if (g.key_type < DFR_U32 || g.key_type > DFR_U32_KV || g.n > DFR_MAX_N) return DFR_ERR_INVALID_ARG;
+  if (!key_type_valid(g.key_type) || g.n > DFR_MAX_N) return DFR_ERR_INVALID_ARG;
   if (g.n > 1) {
     const size_t kb = key_bytes_of(g.key_type);
     if (!g.keys || ((uintptr_t)g.keys % kb) || (g.kbuf && ((uintptr_t)g.kbuf % kb))) return DFR_ERR_INVALID_ARG;
-    if (has_vals(g.key_type) &&
-        (!g.vals || ((uintptr_t)g.vals % 4u) || (g.vbuf && ((uintptr_t)g.vbuf % 4u))))
+    const size_t vb = val_bytes_of(g.key_type);
+    if (has_vals(g.key_type) && (!g.vals || ((uintptr_t)g.vals % vb) || (g.vbuf && ((uintptr_t)g.vbuf % vb))))
       return DFR_ERR_INVALID_ARG;
   }
   if (ws_bytes(g.key_type, g.n, 1u) + scratch_bytes(g) > s->budget) return DFR_ERR_OVER_BUDGET;

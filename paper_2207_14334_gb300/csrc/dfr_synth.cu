@@ -25,7 +25,7 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t s, uint64_t i) {
   return z ^ (z >> 31);
 }
 
-__global__ void k_fill_splitmix64(void* keys, uint32_t* vals, uint64_t n, int wide, uint64_t seed) {
+__global__ void k_fill_splitmix64(void* keys, void* vals, int vwide, uint64_t n, int wide, uint64_t seed) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const uint64_t z = splitmix64_at(seed, i);
@@ -33,7 +33,12 @@ __global__ void k_fill_splitmix64(void* keys, uint32_t* vals, uint64_t n, int wi
       static_cast<uint64_t*>(keys)[i] = z;
     else
       static_cast<uint32_t*>(keys)[i] = (uint32_t)(z >> 32);
-    if (vals) vals[i] = (uint32_t)i;
+    if (vals) {
+      if (vwide)
+        static_cast<uint64_t*>(vals)[i] = i;
+      else
+        static_cast<uint32_t*>(vals)[i] = (uint32_t)i;
+    }
   }
 }
 
@@ -42,19 +47,21 @@ __global__ void k_fill_splitmix64(void* keys, uint32_t* vals, uint64_t n, int wi
 
 using namespace dfr;
 
-extern "C" int dfr_fill_splitmix64(int key_type, void* keys, uint32_t* vals, uint64_t n, uint64_t seed,
+extern "C" int dfr_fill_splitmix64(int key_type, void* keys, void* vals, uint64_t n, uint64_t seed,
                                    dfr_stream_t stream) {
-  if (key_type < DFR_U32 || key_type > DFR_U32_KV) return DFR_ERR_INVALID_ARG;
+  if (!key_type_valid(key_type)) return DFR_ERR_INVALID_ARG;
   if (n == 0) return DFR_OK;
-  const bool wide = key_type == DFR_U64 || key_type == DFR_U64_KV;
-  const bool kv = key_type == DFR_U64_KV || key_type == DFR_U32_KV;
+  const bool wide = key_bytes_of(key_type) == 8u;
+  const bool kv = has_vals(key_type);
+  const size_t vb = val_bytes_of(key_type);
   if (!keys || ((uintptr_t)keys % (wide ? 8u : 4u))) return DFR_ERR_INVALID_ARG;
-  if (kv && (!vals || ((uintptr_t)vals % 4u))) return DFR_ERR_INVALID_ARG;
+  if (kv && (!vals || ((uintptr_t)vals % vb))) return DFR_ERR_INVALID_ARG;
   if (n > DFR_MAX_N) return DFR_ERR_INVALID_ARG;
   const int threads = 256;
   const uint64_t want = (n + threads - 1) / threads;
   const int blocks = (int)(want < 4096 ? want : 4096);
-  k_fill_splitmix64<<<blocks, threads, 0, (cudaStream_t)stream>>>(keys, kv ? vals : nullptr, n, wide ? 1 : 0, seed);
+  k_fill_splitmix64<<<blocks, threads, 0, (cudaStream_t)stream>>>(keys, kv ? vals : nullptr, vb == 8u ? 1 : 0, n,
+                                                                  wide ? 1 : 0, seed);
   rt_count_launch();
   return cudaGetLastError() == cudaSuccess ? DFR_OK : DFR_ERR_CUDA;
 }

@@ -1,0 +1,16 @@
+// dfr_u32_kv64.cu -- instantiation of the DFR sort driver for key type uint32_t, payload uint64_t.
+#include "dfr_host.cuh"
+
+namespace dfr {
+
+int run_u32_kv64(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt) {
+  return run_sort<uint32_t, uint64_t>(a, n, batch, ws, wsb, st, fmt);
+}
+
+size_t ws_u32_kv64(uint64_t ntot, uint32_t narr) { return workspace_bytes<uint32_t, uint64_t>(ntot, narr); }
+
+int graph_u32_kv64(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes) {
+  return build_graph<uint32_t, uint64_t>(a, n, ws, wsb, out, nodes);
+}
+
+}  // namespace dfr

@@ -29,7 +29,7 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 INC = os.path.join(HERE, "csrc", "dfr_tune_table.inc")
 
-KEY_TYPES = ("DFR_U32", "DFR_U64", "DFR_U64_KV", "DFR_U32_KV")  # row order of the C table
+KEY_TYPES = ("DFR_U32", "DFR_U64", "DFR_U64_KV", "DFR_U32_KV", "DFR_U64_KV64", "DFR_U32_KV64")  # row order of the C table
 FIELDS = ("target_log2", "max_bits", "warp_max", "scatter_ctas_per_sm", "ctasort_ctas_per_sm", "schedule")
 
 
@@ -63,16 +63,17 @@ class Case:
         self.keys = torch.empty(total, dtype=kdt, device="cuda")
         self.src = torch.empty_like(self.keys)
         self.kbuf = torch.empty_like(self.keys)
-        self.vals = torch.empty(total, dtype=torch.int32, device="cuda") if kv else None
+        vb = dfr.VAL_BYTES[kt]
+        self.vals = torch.empty(total, dtype=torch.int64 if vb == 8 else torch.int32, device="cuda") if kv else None
         self.vsrc = torch.empty_like(self.vals) if kv else None
         self.vbuf = torch.empty_like(self.vals) if kv else None
         for a in range(count):
             o = a * stride
             dfr.check(dfr.dfr_fill_splitmix64(kt, self.src.data_ptr() + o * kb,
-                                              (self.vsrc.data_ptr() + o * 4) if kv else 0, n, seed + a), "fill")
+                                              (self.vsrc.data_ptr() + o * vb) if kv else 0, n, seed + a), "fill")
         self.segs = [(kt, self.keys.data_ptr() + a * stride * kb,
-                      (self.vals.data_ptr() + a * stride * 4) if kv else 0,
-                      self.kbuf.data_ptr() + a * stride * kb, (self.vbuf.data_ptr() + a * stride * 4) if kv else 0,
+                      (self.vals.data_ptr() + a * stride * vb) if kv else 0,
+                      self.kbuf.data_ptr() + a * stride * kb, (self.vbuf.data_ptr() + a * stride * vb) if kv else 0,
                       n) for a in range(count)]
         self.wsb = dfr.dfr_batch_workspace_bytes(self.segs)
         self.ws = torch.zeros(self.wsb, dtype=torch.uint8, device="cuda")
@@ -144,7 +145,8 @@ def tune(key_types, classes, reps: int, budget_keys: int, schedules=(0, 1), log=
 def write_inc(table, path=INC, note=""):
     default = dict(target_log2=12, max_bits=8, warp_max=512, scatter_ctas_per_sm=0, ctasort_ctas_per_sm=0, schedule=0)
     lines = ["// dfr_tune_table.inc -- the built-in launch plans, one row per key type",
-             "// (DFR_U32, DFR_U64, DFR_U64_KV, DFR_U32_KV) and size class (mean array",
+             "// (" + ", ".join(KEY_TYPES) + ")",
+             "// and size class (mean array",
              "// length 2^<12, [2^12, 2^14), ..., 2^28+).  Fields: target_log2, max_bits,",
              "// warp_max, scatter_ctas_per_sm, ctasort_ctas_per_sm, schedule, reserved x2.",
              "// Written by paper_2207_14334_gb300/tune.py" + (": " + note if note else "") + "."]

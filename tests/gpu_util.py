@@ -33,10 +33,11 @@ def gpu_sort(dfr, keys, vals=None, key_type=None):
     """Sort numpy keys (and payloads) on the GPU; returns numpy results and the
     device status of the call."""
     if key_type is None:
+        wide_vals = vals is not None and vals.dtype.itemsize == 8
         if keys.dtype == np.uint32:
-            key_type = dfr.DFR_U32 if vals is None else dfr.DFR_U32_KV
+            key_type = dfr.DFR_U32 if vals is None else (dfr.DFR_U32_KV64 if wide_vals else dfr.DFR_U32_KV)
         else:
-            key_type = dfr.DFR_U64 if vals is None else dfr.DFR_U64_KV
+            key_type = dfr.DFR_U64 if vals is None else (dfr.DFR_U64_KV64 if wide_vals else dfr.DFR_U64_KV)
     n = keys.size
     s = sorter(dfr, key_type, n)
     dk = dfr.to_device(keys) if n else None
@@ -47,5 +48,5 @@ def gpu_sort(dfr, keys, vals=None, key_type=None):
     s.sort_(dk, dv)
     status = s.device_status()
     k = dfr.to_numpy(dk, keys.dtype)
-    v = None if vals is None else dfr.to_numpy(dv, np.uint32)
+    v = None if vals is None else dfr.to_numpy(dv, np.uint64 if vals.dtype.itemsize == 8 else np.uint32)
     return k, v, status

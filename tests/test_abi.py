@@ -44,7 +44,7 @@ def test_workspace_bytes(lib):
     assert 0 < small < big
     # the workspace stays a modest fraction of the key array at full size
     assert big < 0.5 * (1 << 28) * 4
-    for kt in (dfr.DFR_U64, dfr.DFR_U64_KV, dfr.DFR_U32_KV):
+    for kt in (dfr.DFR_U64, dfr.DFR_U64_KV, dfr.DFR_U32_KV, dfr.DFR_U64_KV64, dfr.DFR_U32_KV64):
         assert dfr.dfr_workspace_bytes(kt, 1 << 20) > 0
     out = ctypes.c_size_t(0)
     assert lib.dfr_workspace_bytes(99, 10, ctypes.byref(out)) == dfr.DFR_ERR_INVALID_ARG
@@ -114,7 +114,7 @@ def test_tune_table_api(lib):
     """Size classes, the built-in table, overrides and their validation (no CUDA call)."""
     assert [dfr.dfr_tune_class(n) for n in (0, 1, 4095, 4096, 16383, 16384, 1 << 20, (1 << 28) - 1, 1 << 28,
                                             1 << 40)] == [0, 0, 0, 1, 1, 2, 5, 8, 9, 9]
-    for kt in (dfr.DFR_U32, dfr.DFR_U64, dfr.DFR_U64_KV, dfr.DFR_U32_KV):
+    for kt in (dfr.DFR_U32, dfr.DFR_U64, dfr.DFR_U64_KV, dfr.DFR_U32_KV, dfr.DFR_U64_KV64, dfr.DFR_U32_KV64):
         for c in range(dfr.DFR_TUNE_CLASSES):
             t = dfr.dfr_tune_get(kt, c)
             assert 6 <= t["target_log2"] <= 13 and 4 <= t["max_bits"] <= 8
@@ -137,8 +137,8 @@ def test_tune_table_api(lib):
 
 
 def test_tuner_writes_a_table_the_library_compiles(tmp_path):
-    """tune.write_inc emits the 4 x DFR_TUNE_CLASSES rows the built-in table
-    expects (the checked-in table is such a file)."""
+    """tune.write_inc emits the (key types) x DFR_TUNE_CLASSES rows the
+    built-in table expects (the checked-in table is such a file)."""
     from paper_2207_14334_gb300 import tune
 
     table = {"DFR_U32": {"3": dict(target_log2=11, max_bits=7, warp_max=256, scatter_ctas_per_sm=2,
@@ -148,12 +148,13 @@ def test_tuner_writes_a_table_the_library_compiles(tmp_path):
     p = tmp_path / "t.inc"
     tune.write_inc(table, path=str(p), note="test")
     body = "".join(l for l in p.read_text().splitlines(True) if not l.startswith("//"))
-    assert body.count("{0, 0}}") == 4 * dfr.DFR_TUNE_CLASSES
+    assert len(tune.KEY_TYPES) == 6
+    assert body.count("{0, 0}}") == len(tune.KEY_TYPES) * dfr.DFR_TUNE_CLASSES
     assert "{11, 7, 256, 2, 1, 0, {0, 0}}" in body
     assert "{12, 8, 512, 0, 0, 2, {0, 0}}" in body
     shipped = open(tune.INC).read()
     assert "".join(l for l in shipped.splitlines(True) if not l.startswith("//")).count("{0, 0}}") == \
-        4 * dfr.DFR_TUNE_CLASSES
+        len(tune.KEY_TYPES) * dfr.DFR_TUNE_CLASSES
 
 
 def test_graph_host_checks(lib):
@@ -186,7 +187,7 @@ def test_workspace_bytes_never_decrease(lib):
     """A workspace sized for n keys must serve every call of fewer keys, also
     across the sizes where the plan switches the scatter geometry (2^22 keys
     in all) or starts to allow the LSD phase (dfr_lsd_min_keys)."""
-    for kt in (dfr.DFR_U32, dfr.DFR_U64, dfr.DFR_U64_KV, dfr.DFR_U32_KV):
+    for kt in (dfr.DFR_U32, dfr.DFR_U64, dfr.DFR_U64_KV, dfr.DFR_U32_KV, dfr.DFR_U64_KV64, dfr.DFR_U32_KV64):
         edges = [1 << 22, dfr.dfr_lsd_min_keys(kt)]
         pts = set([1, 2, 3, 31, 33, 4096, 6145, 8193, 12289, 1 << 20, 1 << 24, 1 << 28, dfr.DFR_MAX_N])
         for e in edges:
@@ -226,7 +227,7 @@ def test_lsd_minimum_and_size_classes(lib):
     [2^(10+2c), 2^(12+2c)); class 0 everything below 2^12, the last class
     2^28 and up."""
     assert dfr.dfr_lsd_min_keys(dfr.DFR_U32) == 256 * 6144
-    for kt in (dfr.DFR_U64, dfr.DFR_U64_KV, dfr.DFR_U32_KV):
+    for kt in (dfr.DFR_U64, dfr.DFR_U64_KV, dfr.DFR_U32_KV, dfr.DFR_U64_KV64, dfr.DFR_U32_KV64):
         assert dfr.dfr_lsd_min_keys(kt) == 256 * 4096
     for c in range(1, dfr.DFR_TUNE_CLASSES - 1):
         lo, hi = 1 << (10 + 2 * c), 1 << (12 + 2 * c)

@@ -83,6 +83,17 @@ for trial in range(8):
     cnt = np.bincount(((k64 >> np.uint64(56)) & np.uint64(255)).astype(np.int64), minlength=256)
     assert orc.overflow_count(k64, 56, cap) == int(np.maximum(cnt - cap, 0).sum())
 assert orc.overflow_count(np.full(100, 7, np.uint32), 0, 10) == 90
+i64 = np.arange(3000, dtype=np.uint64)
+pay = i64 | (((i64 * np.uint64(0x9E3779B1)) & np.uint64(0xFFFFFFFF)) << np.uint64(32))
+for trial in range(20):
+    k64 = g.bit_generator.random_raw(3000).astype(np.uint64) >> np.uint64(int(g.integers(0, 60)))
+    kk, vv = orc.sort_u64_kv64(k64, pay)
+    order = np.argsort(k64, kind="stable")
+    assert np.array_equal(kk, k64[order]) and np.array_equal(vv, pay[order])
+    k32 = (k64 & np.uint64(0xFFFFFFFF)).astype(np.uint32) >> np.uint32(int(g.integers(0, 28)))
+    kk, vv = orc.sort_u32_kv64(k32, pay)
+    order = np.argsort(k32, kind="stable")
+    assert np.array_equal(kk, k32[order]) and np.array_equal(vv, pay[order])
 print("PINS-PASS")
 """
 
@@ -106,6 +117,9 @@ MUTANTS = [
     ("static uint64_t fmt_encode(", "x = x ^ sign;", "x = x ^ (sign >> 1);"),
     ("static uint64_t fmt_decode(", "if (fmt & ORACLE_FMT_DESC) y = y ^ all;", ";"),
     ("static uint64_t fmt_decode(", "if (y & sign) y = y & ~sign;", "if (y & sign) y = y ^ all;"),
+    ("counting_pass_u64_kv64(", "vdst[at] = vsrc[i];", "vdst[at] = (uint32_t)vsrc[i];"),
+    ("counting_pass_u32_kv64(", "vdst[at] = vsrc[i];", "vdst[at] = vsrc[i] & 0xFFFFFFFF00000000ull | (uint32_t)i;"),
+    ("int oracle_sort_u32_kv64(", "vt = vs; vs = vd; vd = vt;", "vt = vs;"),
     ("int oracle_overflow_count(", "if (fill[b] < cap)", "if (fill[b] <= cap)"),
     ("int oracle_overflow_count(", "(unsigned)((key >> shift) & 255u)", "(unsigned)((key >> shift) & 127u)"),
     ("int oracle_overflow_count(", "((const uint32_t*)keys)[i]", "((const uint32_t*)keys)[i] >> 1"),

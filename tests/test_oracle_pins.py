@@ -252,3 +252,51 @@ def test_unsigned_descending_and_bad_format():
     assert np.array_equal(oracle.sort_format(0, 0, a), np.sort(a))
     with pytest.raises(RuntimeError):
         oracle.sort_format(0, 3, a)
+
+
+def wide_payload(n):
+    """64-bit payloads whose high and low halves both vary: the original index
+    in the low half, a per-record pattern in the high half, so a payload cut to
+    32 bits, or moved as two halves from different records, does not survive."""
+    i = np.arange(n, dtype=np.uint64)
+    return i | (((i * np.uint64(0x9E3779B1)) & np.uint64(0xFFFFFFFF)) << np.uint64(32))
+
+
+@pytest.mark.parametrize("n", range(0, 6))
+def test_kv64_exhaustive_vs_insertion_sort(n):
+    """64-bit payloads move with their keys, stably, exactly as a stable
+    insertion sort of (key, original index) records places them."""
+    orc = oracle.default()
+    pay = wide_payload(n)
+    for tup in itertools.product(U64_ALPHABET[:5], repeat=n):
+        want_k, want_i = insertion_sort_pairs(tup)
+        k, v = orc.sort_u64_kv64(np.array(tup, dtype=np.uint64), pay)
+        assert k.tolist() == want_k and v.tolist() == pay[want_i].tolist(), tup
+    for tup in itertools.product(U32_ALPHABET, repeat=n):
+        want_k, want_i = insertion_sort_pairs(tup)
+        k, v = orc.sort_u32_kv64(np.array(tup, dtype=np.uint32), pay)
+        assert k.tolist() == want_k and v.tolist() == pay[want_i].tolist(), tup
+
+
+def test_kv64_random_vs_numpy_stable_and_special_cases():
+    orc = oracle.default()
+    g = np.random.Generator(np.random.PCG64(synth.BASE_SEED + 64))
+    for trial in range(300):
+        n = int(g.integers(0, 3001))
+        k64 = g.bit_generator.random_raw(n).astype(np.uint64) >> np.uint64(int(g.integers(0, 64)))
+        k32 = (k64 & np.uint64(0xFFFFFFFF)).astype(np.uint32) >> np.uint32(int(g.integers(0, 32)))
+        v = g.bit_generator.random_raw(n).astype(np.uint64)
+        kk, vv = orc.sort_u64_kv64(k64, v)
+        order = np.argsort(k64, kind="stable")
+        assert np.array_equal(kk, k64[order]) and np.array_equal(vv, v[order])
+        kk, vv = orc.sort_u32_kv64(k32, v)
+        order = np.argsort(k32, kind="stable")
+        assert np.array_equal(kk, k32[order]) and np.array_equal(vv, v[order])
+    # all-equal keys: the payloads keep their order; reverse distinct keys: reversed
+    n = 5000
+    pay = wide_payload(n)
+    k, v = orc.sort_u64_kv64(np.full(n, 0xDEADBEEFCAFEF00D, np.uint64), pay)
+    assert np.array_equal(v, pay)
+    d = np.arange(n, dtype=np.uint32)[::-1].copy() * np.uint32(97)
+    k, v = orc.sort_u32_kv64(d, pay)
+    assert np.array_equal(k, d[::-1]) and np.array_equal(v, pay[::-1])
