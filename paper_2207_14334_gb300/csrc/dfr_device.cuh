@@ -969,10 +969,11 @@ constexpr size_t scatter_smem_bytes() {
 
 // CTAs per SM the scatter-shaped kernels are compiled for: key-only tiles of
 // up to 16 keys per thread fit three (40 registers); larger key-only tiles,
-// key-value tiles and the estimated LSD pass (EST) take two (64 registers).
-template <class V, int KPT, bool EST>
+// key-value tiles and the estimated LSD pass (EST) take two (64 registers);
+// blocks of 256 threads take twice as many.
+template <class V, int KPT, bool EST, int NT = 512>
 constexpr int scatter_min_blocks() {
-  return (std::is_same<V, NoVal>::value && !EST && KPT <= 16) ? 3 : 2;
+  return ((std::is_same<V, NoVal>::value && !EST && KPT <= 16) ? 3 : 2) * (NT <= 256 ? 2 : 1);
 }
 
 // A segment is dealt at its level unless all its keys are equal or its digit
@@ -1156,7 +1157,7 @@ __device__ __forceinline__ uint32_t look_back(const Ctx& c, uint32_t* status, ui
 // Key-value: stable per-warp ranking in element order, tiles placed in tile
 // order by a single-pass decoupled look-back per digit.
 template <class K, class V, int NT, int KPT>
-__global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false>())) k_scatter(Ctx c, int L) {
+__global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false, NT>())) k_scatter(Ctx c, int L) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr uint32_t TILE = (uint32_t)NT * KPT;
   constexpr int NW = NT / 32;

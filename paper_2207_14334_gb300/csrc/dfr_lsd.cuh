@@ -62,7 +62,7 @@ constexpr size_t lsd_smem_bytes() {
 // D0 back into the array).  Persistent: CTAs claim tiles in increasing order.
 // EST: the estimated first pass of mode 2 (also counts D0 and the OR/AND).
 template <class K, class V, int NT, int KPT, int PASS, bool EST>
-__global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, EST>())) k_lsd_pass(Ctx c) {
+__global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, EST, NT>())) k_lsd_pass(Ctx c) {
   static_assert(PASS == 0 || !EST, "only the first pass is estimated");
   constexpr int pass = PASS;
   constexpr bool KV = !std::is_same<V, NoVal>::value;
