@@ -357,7 +357,9 @@ def dominant_roofline(prof, stats, rec, peak, peak_kind):
     move records (the scatter and the CTA sort): algorithmic bytes = a read
     and a write of every record it handles, over its measured time."""
     moved = {"scatter": 2 * rec * sum(stats["level_keys"]),
-             "ctasort": 2 * rec * stats["cta_keys"]}
+             "ctasort": 2 * rec * stats["cta_keys"],
+             # the whole call as one persistent launch: every byte of the sort
+             "persist": stats["model_bytes"]}
     cand = [k for k in moved if k in prof and prof[k][0] > 0]
     if not cand:
         return None
@@ -899,15 +901,17 @@ def run_plain(args, wl, dfr, dev, world, rank, emit=True):
     # passes (when an LSD schedule dealt the top digits) or the CTA sort --
     # algorithmic bytes = a read and a write of every record it handles.
     cta_keys = sum(p["cta_keys"] for p in plan.values())
+    # A call run as one persistent launch (k_persist) moves every byte of the
+    # sort in that launch: its algorithmic bytes are the plan's model bytes.
     cands = {"k_scatter": ("scatter", scatter_keys), "k_lsd_pass": ("lsd_pass", lsd_keys),
-             "k_ctasort": ("ctasort", cta_keys)}
+             "k_ctasort": ("ctasort", cta_keys), "k_persist": ("persist", None)}
     dom_kernel = max((k for k in cands if cands[k][0] in prof), key=lambda k: prof[cands[k][0]][0])
     dom_ms, dom_launches = prof[cands[dom_kernel][0]]
     dom_keys = cands[dom_kernel][1]
-    dom_bytes = 2 * rec * dom_keys
+    dom_bytes = 2 * rec * dom_keys if dom_keys is not None else sum(p["model_bytes"] for p in plan.values())
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else 0.0
     traffic = None
-    per_key = traffic_per_key(dom_kernel) if not kv else None
+    per_key = traffic_per_key(dom_kernel) if not kv and dom_keys is not None else None
     if per_key is not None:
         traffic = per_key * dom_keys / max(1, dom_launches)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

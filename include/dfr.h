@@ -161,7 +161,8 @@ typedef struct {
                                                           sorted the array instead */
     uint32_t root_read;                                /* 1: the root count read the keys (0 when the estimated
                                                           deal counted them) */
-    uint32_t reserved2;
+    uint32_t persistent;                               /* 1: the call ran as one persistent launch
+                                                          (DFR_LAUNCH_*) */
 } dfr_stats_t;
 
 /* dfr_get_stats -- wait for `stream` and copy the counters of the last call
@@ -389,8 +390,28 @@ typedef struct {
     uint32_t ctasort_ctas_per_sm;  /* CTA-sort grid: CTAs per SM, 0 = as many as fit */
     uint32_t schedule;             /* how a single array sorts its top two digits (DFR_SCHED_*); batches
                                       always use DFR_SCHED_MSD */
-    uint32_t reserved[2];          /* zero */
+    uint32_t launch;               /* how the call is launched (DFR_LAUNCH_*) */
+    uint32_t reserved;             /* zero */
 } dfr_tune_t;
+
+/*
+ * Launch forms of a plain call or a dfr_sort_batch call (the served form
+ * always uses the level sequence).  Both give the same result.
+ *   DFR_LAUNCH_AUTO        one persistent launch for calls of fewer than
+ *                          DFR_PERSIST_AUTO_KEYS keys in all, the level
+ *                          sequence otherwise;
+ *   DFR_LAUNCH_LEVELS      the level sequence: every phase of every level is
+ *                          its own kernel (about 24 launches per call);
+ *   DFR_LAUNCH_PERSISTENT  one persistent, cooperative launch in which every
+ *                          CTA pulls the count, deal, classification, diverted
+ *                          bucket and copy-back items of all arrays from device
+ *                          queues, phases separated by bounded grid-wide
+ *                          barriers (a wait that runs out records
+ *                          DFR_ERR_TIMEOUT), levels run until none is left.
+ * The LSD schedules of the top digits always run as the level sequence.
+ */
+enum dfr_launch { DFR_LAUNCH_AUTO = 0, DFR_LAUNCH_LEVELS = 1, DFR_LAUNCH_PERSISTENT = 2 };
+#define DFR_PERSIST_AUTO_KEYS ((uint64_t)1 << 22)
 
 /*
  * Schedules of the top digits (paper, Section "Diverting Fast Radix").
@@ -449,9 +470,10 @@ int dfr_fill_splitmix64(int key_type, void* keys, void* vals, uint64_t n, uint64
  * dfr_set_debug -- process-wide debug knobs (not for production use).
  *   spin_limit     iterations a device-side wait may spin before it gives up
  *                  and records DFR_ERR_TIMEOUT (0 = default limit);
- *   force_timeout  1 = the decoupled look-back waits on a status word that no
- *                  tile ever sets, so it must time out (tests the timeout path
- *                  without hanging anything); 0 = normal.
+ *   force_timeout  1 = the decoupled look-back and the persistent launch's
+ *                  grid-wide barriers wait on a status word that nothing ever
+ *                  sets, so they must time out (tests the timeout path without
+ *                  hanging anything); 0 = normal.
  */
 int dfr_set_debug(uint32_t spin_limit, int force_timeout);
 
@@ -460,7 +482,7 @@ int dfr_set_debug(uint32_t spin_limit, int force_timeout);
  * device, returns per-kind totals and clears them.  Kinds are listed by
  * dfr_profile_kind_name(). */
 int dfr_profile_enable(int on);
-#define DFR_PROFILE_KINDS 13
+#define DFR_PROFILE_KINDS 14
 int dfr_profile_read(double* ms_total /*[DFR_PROFILE_KINDS]*/, uint64_t* launches /*[DFR_PROFILE_KINDS]*/);
 const char* dfr_profile_kind_name(int kind);
 

@@ -46,7 +46,7 @@ DFR_U32_KV64 = 5
 
 DFR_MAX_N = (1 << 30) - 1
 DFR_NOALLOC_MAX_N = 1 << 20
-DFR_PROFILE_KINDS = 13
+DFR_PROFILE_KINDS = 14
 DFR_STATS_MAX_LEVELS = 16
 DFR_SERVER_MAX_STREAMS = 64
 DFR_SERVER_MAX_INFLIGHT = 64
@@ -60,6 +60,10 @@ DFR_TUNE_WARP_MAX = 512
 DFR_SCHED_MSD = 0
 DFR_SCHED_LSD = 1
 DFR_SCHED_DFR = 2
+DFR_LAUNCH_AUTO = 0
+DFR_LAUNCH_LEVELS = 1
+DFR_LAUNCH_PERSISTENT = 2
+DFR_PERSIST_AUTO_KEYS = 1 << 22
 
 KEY_BYTES = {DFR_U32: 4, DFR_U64: 8, DFR_U64_KV: 8, DFR_U32_KV: 4, DFR_U64_KV64: 8, DFR_U32_KV64: 4}
 VAL_BYTES = {DFR_U32: 0, DFR_U64: 0, DFR_U64_KV: 4, DFR_U32_KV: 4, DFR_U64_KV64: 8, DFR_U32_KV64: 8}
@@ -92,15 +96,17 @@ class dfr_stats_t(ctypes.Structure):
                 ("const_buckets", _u64), ("const_keys", _u64), ("copy_keys", _u64), ("model_bytes", _u64),
                 ("wsort_buckets", _u64), ("wsort_keys", _u64), ("device_error_site", _u32), ("schedule", _u32),
                 ("group_buckets", _u64), ("lsd_keys", _u64), ("est_overflow", _u64), ("est_capacity", _u32),
-                ("est_aborted", _u32), ("root_read", _u32), ("reserved2", _u32)]
+                ("est_aborted", _u32), ("root_read", _u32), ("persistent", _u32)]
 
 
 class dfr_tune_t(ctypes.Structure):
     _fields_ = [("target_log2", _u32), ("max_bits", _u32), ("warp_max", _u32), ("scatter_ctas_per_sm", _u32),
-                ("ctasort_ctas_per_sm", _u32), ("schedule", _u32), ("reserved", _u32 * 2)]
+                ("ctasort_ctas_per_sm", _u32), ("schedule", _u32), ("launch", _u32), ("reserved", _u32)]
 
 
-TUNE_FIELDS = ("target_log2", "max_bits", "warp_max", "scatter_ctas_per_sm", "ctasort_ctas_per_sm", "schedule")
+TUNE_FIELDS = ("target_log2", "max_bits", "warp_max", "scatter_ctas_per_sm", "ctasort_ctas_per_sm", "schedule",
+               "launch")
+_TUNE_OPTIONAL = ("schedule", "launch")  # fields a plan may leave out (0 = DFR_SCHED_MSD, DFR_LAUNCH_AUTO)
 
 _SIGNATURES = {
     "dfr_workspace_bytes": (ctypes.c_int, [ctypes.c_int, _u64, ctypes.POINTER(_sz)]),
@@ -186,7 +192,7 @@ def _apply_env_config(lib) -> None:
                 raise ValueError("DFR_TUNE_FILE %s: unknown key type %r" % (path, name))
             for c, entry in classes.items():
                 try:
-                    t = dfr_tune_t(*(int(entry.get(f, 0) if f == "schedule" else entry[f]) for f in TUNE_FIELDS))
+                    t = dfr_tune_t(*(int(entry.get(f, 0) if f in _TUNE_OPTIONAL else entry[f]) for f in TUNE_FIELDS))
                     c = int(c)
                 except (KeyError, TypeError, ValueError, AttributeError) as e:
                     raise ValueError("DFR_TUNE_FILE %s: entry %s / class %s: %r" % (path, name, c, e)) from None
@@ -421,8 +427,9 @@ def dfr_tune_get(key_type: int, size_class: int) -> dict:
 
 def dfr_tune_set(key_type: int, size_class: int, tune: dict) -> int:
     """Override one entry of the launch-plan table (fields as dfr_tune_get;
-    a missing "schedule" means DFR_SCHED_MSD)."""
-    t = dfr_tune_t(*(int(tune.get(f, 0) if f == "schedule" else tune[f]) for f in TUNE_FIELDS))
+    a missing "schedule" means DFR_SCHED_MSD, a missing "launch"
+    DFR_LAUNCH_AUTO)."""
+    t = dfr_tune_t(*(int(tune.get(f, 0) if f in _TUNE_OPTIONAL else tune[f]) for f in TUNE_FIELDS))
     return load().dfr_tune_set(int(key_type), int(size_class), ctypes.byref(t))
 
 

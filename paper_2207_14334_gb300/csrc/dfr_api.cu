@@ -54,7 +54,8 @@ bool tune_valid(const dfr_tune_t& t) {
   if (t.warp_max < DFR_TUNE_WARP_MIN || t.warp_max > DFR_TUNE_WARP_MAX) return false;
   if (t.scatter_ctas_per_sm > 4 || t.ctasort_ctas_per_sm > 4) return false;
   if (t.schedule > DFR_SCHED_DFR) return false;
-  return t.reserved[0] == 0 && t.reserved[1] == 0;
+  if (t.launch > DFR_LAUNCH_PERSISTENT) return false;
+  return t.reserved == 0;
 }
 
 }  // namespace
@@ -126,14 +127,14 @@ int map_device_status(uint32_t err) {
 }
 
 int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st,
-              int fmt) {
+              int fmt, bool persist_ok) {
   switch (key_type) {
-    case DFR_U32: return run_u32(a, n, batch, ws, wsb, st, fmt);
-    case DFR_U32_KV: return run_u32_kv(a, n, batch, ws, wsb, st, fmt);
-    case DFR_U64_KV64: return run_u64_kv64(a, n, batch, ws, wsb, st, fmt);
-    case DFR_U32_KV64: return run_u32_kv64(a, n, batch, ws, wsb, st, fmt);
-    case DFR_U64: return run_u64(a, n, batch, ws, wsb, st, fmt);
-    case DFR_U64_KV: return run_u64_kv(a, n, batch, ws, wsb, st, fmt);
+    case DFR_U32: return run_u32(a, n, batch, ws, wsb, st, fmt, persist_ok);
+    case DFR_U32_KV: return run_u32_kv(a, n, batch, ws, wsb, st, fmt, persist_ok);
+    case DFR_U64_KV64: return run_u64_kv64(a, n, batch, ws, wsb, st, fmt, persist_ok);
+    case DFR_U32_KV64: return run_u32_kv64(a, n, batch, ws, wsb, st, fmt, persist_ok);
+    case DFR_U64: return run_u64(a, n, batch, ws, wsb, st, fmt, persist_ok);
+    case DFR_U64_KV: return run_u64_kv(a, n, batch, ws, wsb, st, fmt, persist_ok);
     default: return DFR_ERR_INVALID_ARG;
   }
 }
@@ -188,36 +189,36 @@ int dfr_workspace_bytes(int key_type, uint64_t n, size_t* bytes) {
 
 int dfr_sort_u32(uint32_t* keys, uint32_t* buf, uint64_t n, void* ws, size_t ws_bytes, dfr_stream_t stream) {
   const HostArr a{keys, buf, nullptr, nullptr, n};
-  return run_u32(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED);
+  return run_u32(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED, true);
 }
 
 int dfr_sort_u64(uint64_t* keys, uint64_t* buf, uint64_t n, void* ws, size_t ws_bytes, dfr_stream_t stream) {
   const HostArr a{keys, buf, nullptr, nullptr, n};
-  return run_u64(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED);
+  return run_u64(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED, true);
 }
 
 int dfr_sort_u64_kv(uint64_t* keys, uint32_t* vals, uint64_t* kbuf, uint32_t* vbuf, uint64_t n, void* ws,
                     size_t ws_bytes, dfr_stream_t stream) {
   const HostArr a{keys, kbuf, vals, vbuf, n};
-  return run_u64_kv(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED);
+  return run_u64_kv(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED, true);
 }
 
 int dfr_sort_u32_kv(uint32_t* keys, uint32_t* vals, uint32_t* kbuf, uint32_t* vbuf, uint64_t n, void* ws,
                     size_t ws_bytes, dfr_stream_t stream) {
   const HostArr a{keys, kbuf, vals, vbuf, n};
-  return run_u32_kv(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED);
+  return run_u32_kv(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED, true);
 }
 
 int dfr_sort_u64_kv64(uint64_t* keys, uint64_t* vals, uint64_t* kbuf, uint64_t* vbuf, uint64_t n, void* ws,
                       size_t ws_bytes, dfr_stream_t stream) {
   const HostArr a{keys, kbuf, vals, vbuf, n};
-  return run_u64_kv64(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED);
+  return run_u64_kv64(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED, true);
 }
 
 int dfr_sort_u32_kv64(uint32_t* keys, uint64_t* vals, uint32_t* kbuf, uint64_t* vbuf, uint64_t n, void* ws,
                       size_t ws_bytes, dfr_stream_t stream) {
   const HostArr a{keys, kbuf, vals, vbuf, n};
-  return run_u32_kv64(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED);
+  return run_u32_kv64(&a, 1u, false, ws, ws_bytes, (cudaStream_t)stream, DFR_FMT_UNSIGNED, true);
 }
 
 int dfr_last_device_status(const void* ws, dfr_stream_t stream, int* status) {
@@ -281,6 +282,7 @@ int dfr_get_stats(const void* ws, dfr_stream_t stream, dfr_stats_t* out) {
   out->est_capacity = h.est_cap;
   out->est_aborted = h.est_abort;
   out->root_read = h.n_total ? (h.root_skipped ? 0u : 1u) : 0u;
+  out->persistent = h.persist;
   out->wsort_keys = h.wsort_keys;
   return DFR_OK;
 }
@@ -439,7 +441,7 @@ const char* dfr_profile_kind_name(int kind) {
   static const char* names[DFR_PROFILE_KINDS] = {"init",     "root_count", "root_classify", "level_count",
                                                   "scatter",  "classify",   "ctasort",       "copy",
                                                   "h2d",      "warpsort",     "keyfmt",        "lsd_pass",
-                                                  "lsd_plan"};
+                                                  "lsd_plan", "persist"};
   return (kind >= 0 && kind < DFR_PROFILE_KINDS) ? names[kind] : "unknown";
 }
 

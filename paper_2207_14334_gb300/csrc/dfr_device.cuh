@@ -83,7 +83,7 @@ constexpr bool two_cta_queues() {
 enum : uint32_t { DERR_TIMEOUT = 1u, DERR_BOUNDS = 2u, DERR_CAPACITY = 4u };
 enum : uint32_t {
   ERR_SITE_SCATTER_STAGE = 1u, ERR_SITE_SCATTER_WRITE, ERR_SITE_CTASORT_STAGE, ERR_SITE_WARPSORT_STAGE,
-  ERR_SITE_LOOKBACK, ERR_SITE_LSD_STAGE, ERR_SITE_LSD_WRITE, ERR_SITE_CLASSIFY
+  ERR_SITE_LOOKBACK, ERR_SITE_LSD_STAGE, ERR_SITE_LSD_WRITE, ERR_SITE_CLASSIFY, ERR_SITE_GRID_SYNC
 };
 constexpr uint32_t NO_OWNER = 0xffffffffu;  // tile-owner entry of a tile that must be skipped
 // SEG_PREDEALT: a level-0 segment made by the LSD top phase, whose keys are
@@ -172,6 +172,9 @@ struct Ctl {
   uint32_t est_cap;       // estimated bucket size of the estimated deal
   unsigned long long lsd_keys;      // keys dealt by the LSD passes (both passes)
   unsigned long long est_overflow;  // keys the estimated deal sent to an overflow region
+  // one persistent launch (k_persist): grid-barrier arrivals (only grow) and
+  // the number of barriers completed; 1 once the kernel ran
+  uint32_t gbar_count, gbar_gen, persist, pad1;
   LevelCtl lv[MAXLV + 1];
 };
 
@@ -675,11 +678,9 @@ __device__ __forceinline__ void atomic_or_key(K* p, K v) {
 // When the estimated deal already counted the keys (LSD mode 2), it does
 // nothing.
 template <class K, int NT, int TILE, bool TWO>
-__global__ void __launch_bounds__(NT) k_root_count(Ctx c, uint32_t root_tiles, uint32_t* h2) {
-  constexpr int NW = NT / 32;
+__device__ __forceinline__ void root_count_body(const Ctx& c, uint32_t root_tiles, uint32_t* h2, uint32_t* s_h,
+                                                uint32_t* s_h2) {
   constexpr uint32_t TOP = 8 * sizeof(K) - RB;
-  __shared__ uint32_t s_h[NW * M];
-  __shared__ uint32_t s_h2[TWO ? NW * M : 1];
   if (c.lsd_mode == 2u && ld_relaxed(&c.lsd->on) != 0u) {
     if (blockIdx.x == 0 && threadIdx.x == 0) c.ctl->root_skipped = 1u;
     return;
@@ -734,6 +735,13 @@ __global__ void __launch_bounds__(NT) k_root_count(Ctx c, uint32_t root_tiles, u
   flush();
 }
 
+template <class K, int NT, int TILE, bool TWO>
+__global__ void __launch_bounds__(NT) k_root_count(Ctx c, uint32_t root_tiles, uint32_t* h2) {
+  __shared__ uint32_t s_h[(NT / 32) * M];
+  __shared__ uint32_t s_h2[TWO ? (NT / 32) * M : 1];
+  root_count_body<K, NT, TILE, TWO>(c, root_tiles, h2, s_h, s_h2);
+}
+
 // Key formats: the order-preserving bijection between a key's bits and the
 // unsigned value the sort orders by -- two's complement: flip the sign bit;
 // IEEE 754 totalOrder: flip every bit of a negative value, set the sign bit
@@ -765,8 +773,8 @@ __device__ __forceinline__ K fmt_from_order(K y, uint32_t fmt) {
 // `single`: the one array is a0 (the descriptor table is not in the
 // workspace yet); else the arrays are the workspace's descriptor table.
 template <class K, int NT, int TILE>
-__global__ void __launch_bounds__(NT) k_keyfmt(Ctx c, ArrDesc a0, uint32_t single, uint32_t root_tiles, uint32_t fmt,
-                                               uint32_t encode) {
+__device__ __forceinline__ void keyfmt_body(const Ctx& c, const ArrDesc& a0, uint32_t single, uint32_t root_tiles,
+                                            uint32_t fmt, uint32_t encode) {
   for (uint32_t t = blockIdx.x; t < root_tiles; t += gridDim.x) {
     uint32_t lo = 0;
     if (!single) {
@@ -787,9 +795,16 @@ __global__ void __launch_bounds__(NT) k_keyfmt(Ctx c, ArrDesc a0, uint32_t singl
   }
 }
 
-// Root classification, one CTA (256 threads) per array.
-template <class K, class V, int TILE, int TCTA, int WCAP>
-__global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long n_total) {
+template <class K, int NT, int TILE>
+__global__ void __launch_bounds__(NT) k_keyfmt(Ctx c, ArrDesc a0, uint32_t single, uint32_t root_tiles, uint32_t fmt,
+                                               uint32_t encode) {
+  keyfmt_body<K, NT, TILE>(c, a0, single, root_tiles, fmt, encode);
+}
+
+// Root classification, one CTA per array (NTB >= 256 threads: one per top
+// digit for the histogram copy).
+template <class K, class V, int TILE, int TCTA, int WCAP, int NTB>
+__device__ __forceinline__ void root_classify_body(const Ctx& c, unsigned long long n_total) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr int W = 8 * sizeof(K);
   __shared__ uint32_t s_seg, s_ts, s_ok;
@@ -880,15 +895,22 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
           if ((x << sd) < (uint32_t)M)
             for (uint32_t y = x << sd; y < ((x + 1) << sd); ++y) h += root[a].hist[y];
         }
-        c.hist[0][(size_t)s * M + threadIdx.x] = h;
-        if constexpr (!KV) c.cur[0][(size_t)s * M + threadIdx.x] = 0u;
+        if (threadIdx.x < (uint32_t)M) {
+          c.hist[0][(size_t)s * M + threadIdx.x] = h;
+          if constexpr (!KV) c.cur[0][(size_t)s * M + threadIdx.x] = 0u;
+        }
       }
       const uint32_t owner = s_ok ? s : NO_OWNER;
       const uint32_t ntc = ts < c.tilecap ? min(nt, c.tilecap - ts) : 0u;
-      for (uint32_t i = threadIdx.x; i < ntc; i += 256) c.tile_owner[ts + i] = owner;
+      for (uint32_t i = threadIdx.x; i < ntc; i += NTB) c.tile_owner[ts + i] = owner;
     }
     __syncthreads();
   }
+}
+
+template <class K, class V, int TILE, int TCTA, int WCAP>
+__global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long n_total) {
+  root_classify_body<K, V, TILE, TCTA, WCAP, 256>(c, n_total);
 }
 
 // Level count: per segment of this level, the histogram of its digit window
@@ -897,9 +919,7 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
 // of the level.  Warp-granular like k_root_count: private counters flushed per
 // segment.
 template <class K, bool KV, int NT, int TILE>
-__global__ void __launch_bounds__(NT) k_level_count(Ctx c, int L) {
-  constexpr int NW = NT / 32;
-  __shared__ uint32_t s_h[NW * M];
+__device__ __forceinline__ void level_count_body(const Ctx& c, int L, uint32_t* s_h) {
   LevelCtl* lc = &c.ctl->lv[L];
   const uint32_t ntiles = min(lc->ntiles, c.tilecap);
   Seg* segs = ((L & 1) ? c.segs[1] : c.segs[0]);
@@ -955,6 +975,12 @@ __global__ void __launch_bounds__(NT) k_level_count(Ctx c, int L) {
   }
   flush();
   if (lane == 0 && keys_read) atomicAdd(&lc->hist_keys, keys_read);
+}
+
+template <class K, bool KV, int NT, int TILE>
+__global__ void __launch_bounds__(NT) k_level_count(Ctx c, int L) {
+  __shared__ uint32_t s_h[(NT / 32) * M];
+  level_count_body<K, KV, NT, TILE>(c, L, s_h);
 }
 
 template <class K, class V, int NT, int KPT>
@@ -1157,7 +1183,7 @@ __device__ __forceinline__ uint32_t look_back(const Ctx& c, uint32_t* status, ui
 // Key-value: stable per-warp ranking in element order, tiles placed in tile
 // order by a single-pass decoupled look-back per digit.
 template <class K, class V, int NT, int KPT>
-__global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false, NT>())) k_scatter(Ctx c, int L) {
+__device__ __forceinline__ void scatter_body(const Ctx& c, int L) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr uint32_t TILE = (uint32_t)NT * KPT;
   constexpr int NW = NT / 32;
@@ -1342,6 +1368,11 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false, NT>()))
   }
 }
 
+template <class K, class V, int NT, int KPT>
+__global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false, NT>())) k_scatter(Ctx c, int L) {
+  scatter_body<K, V, NT, KPT>(c, L);
+}
+
 // Classification of one level, one CTA (256 threads = one per digit) per
 // segment.  A constant segment is finished (copied back if it sits in the
 // buffer); a segment whose window held no varying bit is passed to the next
@@ -1349,8 +1380,8 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false, NT>()))
 // a dealt segment every bucket is classified by size against the diversion
 // thresholds (Section "Analysis", N_d): tiny buckets are sorted here by warps,
 // mid-size ones queued for k_ctasort, large ones become next-level segments.
-template <class K, class V, int TILE, int TCTA, int WCAP>
-__global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
+template <class K, class V, int TILE, int TCTA, int WCAP, int NTB>
+__device__ __forceinline__ void classify_body(const Ctx& c, int L) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_tiny_n, s_new_n;
@@ -1372,6 +1403,7 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
   uint32_t* cur_n = ((L & 1) ? c.cur[0] : c.cur[1]);
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t d = threadIdx.x;
+  const bool dig = d < (uint32_t)M;  // one thread per digit
 
   // Append one next-level segment and record its tile range for the owner
   // fill.  Called by one thread.
@@ -1451,7 +1483,7 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
         }
       }
     } else {
-      const uint32_t cnt = hist[(size_t)s * M + d];
+      const uint32_t cnt = dig ? hist[(size_t)s * M + d] : 0u;
       uint32_t tot = 0;
       const uint32_t excl = scan256(cnt, s_scan, &tot);
       // A histogram that does not add up to the segment (only after a failed
@@ -1485,8 +1517,10 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
         // hence adjacent in memory and ordered) are joined into runs of at
         // most TCTA keys and each run is sorted as one item -- sorting the run
         // sorts every bucket in it, and equal keys never span two buckets.
-        s_bcnt[d] = cnt > (uint32_t)TCTA ? 0xffffffffu : cnt;
-        s_boff[d] = off;
+        if (dig) {
+          s_bcnt[d] = cnt > (uint32_t)TCTA ? 0xffffffffu : cnt;
+          s_boff[d] = off;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
           // (a run of one bucket varies below the window; one of several
@@ -1596,13 +1630,13 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
     // New segments / copy items: clear histogram slots, fill tile-owner maps.
     const uint32_t nn = s_new_n;
     for (uint32_t i = 0; i < nn; ++i) {
-      if (s_new_zero[i] != NO_OWNER) {
+      if (dig && s_new_zero[i] != NO_OWNER) {
         hist_n[(size_t)s_new_zero[i] * M + threadIdx.x] = 0u;
         if constexpr (!KV) cur_n[(size_t)s_new_zero[i] * M + threadIdx.x] = 0u;
       }
       uint32_t* owner = s_new_copy[i] ? c.copy_owner : c.tile_owner;
       const uint32_t id = s_new_owner[i];
-      for (uint32_t x = threadIdx.x; x < s_new_nt[i]; x += 256) owner[s_new_ts[i] + x] = id;
+      for (uint32_t x = threadIdx.x; x < s_new_nt[i]; x += NTB) owner[s_new_ts[i] + x] = id;
     }
     // Tiny buckets: one warp each.
     const uint32_t tn = s_tiny_n;
@@ -1612,7 +1646,7 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
       const K* psrc = reinterpret_cast<const K*>(pout ? ad.buf : ad.keys);
       using VT = typename ValT<V>::type;
       const VT* pvsrc = reinterpret_cast<const VT*>(pout ? ad.vbuf : ad.vals);
-      for (uint32_t i = warp; i < tn; i += 8) {
+      for (uint32_t i = warp; i < tn; i += NTB / 32) {
         const uint32_t o = s_tiny_off[i];
         const uint32_t len = s_tiny_len[i] & 0x7fffffffu;
         if (s_tiny_len[i] & 0x80000000u) {
@@ -1647,6 +1681,11 @@ __global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
     }
     __syncthreads();
   }
+}
+
+template <class K, class V, int TILE, int TCTA, int WCAP>
+__global__ void __launch_bounds__(256) k_classify(Ctx c, int L) {
+  classify_body<K, V, TILE, TCTA, WCAP, 256>(c, L);
 }
 
 // Diversion sort of mid-size buckets: one CTA per bucket, writing the final
@@ -2014,7 +2053,7 @@ constexpr int ctasort_min_blocks() {
 // `second`: sort the second queue (buckets the u32 key-only fast CTA sort
 // handed over) instead of the classifier's queue.
 template <class K, class V, int NT, int KPT>
-__global__ void __launch_bounds__(NT, (ctasort_min_blocks<K, V, NT>())) k_ctasort(Ctx c, int second) {
+__device__ __forceinline__ void ctasort_body(const Ctx& c, int second) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr uint32_t CAP = (uint32_t)NT * KPT;
   constexpr int NW = NT / 32;
@@ -2081,6 +2120,11 @@ __global__ void __launch_bounds__(NT, (ctasort_min_blocks<K, V, NT>())) k_ctasor
   }
 }
 
+template <class K, class V, int NT, int KPT>
+__global__ void __launch_bounds__(NT, (ctasort_min_blocks<K, V, NT>())) k_ctasort(Ctx c, int second) {
+  ctasort_body<K, V, NT, KPT>(c, second);
+}
+
 // Exclusive scan, in place, of a warp's M = 256 counters (lane l owns
 // counters 8l..8l+7); returns the largest counter.  Call with the whole warp.
 __device__ __forceinline__ uint32_t warp_scan_counters(uint32_t* wh) {
@@ -2118,7 +2162,7 @@ constexpr size_t warpsort_warp_bytes() {
 // buckets of skewed inputs do not pay a whole CTA each.  Ranking as in
 // k_ctasort (stable except the first pass of a key-only sort).
 template <class K, class V, int WPB, int WKPT>
-__global__ void __launch_bounds__(WPB * 32) k_warpsort(Ctx c) {
+__device__ __forceinline__ void warpsort_body(const Ctx& c) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   constexpr uint32_t WCAP = 32u * WKPT;
   constexpr int W = 8 * sizeof(K);
@@ -2283,10 +2327,15 @@ __global__ void __launch_bounds__(WPB * 32) k_warpsort(Ctx c) {
   }
 }
 
+template <class K, class V, int WPB, int WKPT>
+__global__ void __launch_bounds__(WPB * 32) k_warpsort(Ctx c) {
+  warpsort_body<K, V, WPB, WKPT>(c);
+}
+
 // Write-back of large constant buckets that ended in buf: the keys are a fill
 // of the bucket's single value, the payloads are copied.
 template <class K, class V, int NT, int TILE>
-__global__ void __launch_bounds__(NT) k_copy(Ctx c) {
+__device__ __forceinline__ void copy_body(const Ctx& c) {
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   __shared__ uint32_t s_t;
   Ctl* ctl = c.ctl;
@@ -2317,6 +2366,11 @@ __global__ void __launch_bounds__(NT) k_copy(Ctx c) {
     }
     __syncthreads();
   }
+}
+
+template <class K, class V, int NT, int TILE>
+__global__ void __launch_bounds__(NT) k_copy(Ctx c) {
+  copy_body<K, V, NT, TILE>(c);
 }
 
 }  // namespace dfr

@@ -15,6 +15,7 @@
 #include "dfr_ctasort32.cuh"
 #include "dfr_device.cuh"
 #include "dfr_lsd.cuh"
+#include "dfr_persist.cuh"
 #include "dfr_scatter_bulk.cuh"
 
 namespace dfr {
@@ -40,7 +41,7 @@ int rt_sms();
 dfr_tune_t rt_tune(int key_type, uint64_t mean_keys);
 
 enum ProfKind { PK_INIT = 0, PK_ROOT_COUNT, PK_ROOT_CLASSIFY, PK_LEVEL_COUNT, PK_SCATTER, PK_CLASSIFY, PK_CTASORT,
-                PK_COPY, PK_H2D, PK_WARPSORT, PK_KEYFMT, PK_LSD_PASS, PK_LSD_PLAN };
+                PK_COPY, PK_H2D, PK_WARPSORT, PK_KEYFMT, PK_LSD_PASS, PK_LSD_PLAN, PK_PERSIST };
 
 // Properties of the key types of the C interface (enum dfr_key_type).
 inline bool key_type_valid(int kt) { return kt >= DFR_U32 && kt <= DFR_U32_KV64; }
@@ -301,7 +302,7 @@ size_t workspace_bytes(uint64_t ntot, uint32_t narr) {
 
 // Persistent grid sizes of every kernel of one key type on one device.
 struct Grids {
-  int rc, rcl, lc, sc, cl, cs, ws, cp, kf, lp, le, rc2, lp1, cs32;
+  int rc, rcl, lc, sc, cl, cs, ws, cp, kf, lp, le, rc2, lp1, cs32, ps;
 };
 
 // The tuning entry's CTAs-per-SM caps applied to the persistent grids.
@@ -376,6 +377,10 @@ struct Kernels {
   static_assert(!FAST32 || C32::CAP == (uint32_t)TCTA, "both CTA sorts take buckets up to the diversion threshold");
   static constexpr size_t cs32_smem = ctasort32_smem_bytes<CS32_NC, CS32_NV, CS32_STAGES>();
   static constexpr auto ctasort32 = k_ctasort32<CS32_NC, CS32_NV, CS32_STAGES, CS32_MINB>;
+  // the whole call as one persistent, cooperative launch (dfr_persist.cuh)
+  static_assert(SNT == CNT, "the persistent form runs every phase in one block size");
+  using PC = PersistCfg<K, V, SNT, SKPT, CKPT, WKPT>;
+  static constexpr auto persist = k_persist<K, V, SNT, SKPT, CKPT, WKPT>;
 
   // grid_of(kernel, threads, dynamic smem) -> persistent grid (or < 0 on error)
   template <class GridOf>
@@ -394,7 +399,8 @@ struct Kernels {
     g->le = grid_of((const void*)lsd_est, SNT, lp_smem);
     g->rc2 = grid_of((const void*)root_count2, SNT, (size_t)0);
     g->cs32 = FAST32 ? grid_of((const void*)ctasort32, CS32_NT, cs32_smem) : 1;
-    return g->cs32 > 0 && g->rc > 0 && g->rcl > 0 && g->lc > 0 && g->sc > 0 && g->cl > 0 && g->cs > 0 && g->ws > 0 && g->cp > 0 &&
+    g->ps = grid_of((const void*)persist, PC::NT, PC::smem);
+    return g->ps > 0 && g->cs32 > 0 && g->rc > 0 && g->rcl > 0 && g->lc > 0 && g->sc > 0 && g->cl > 0 && g->cs > 0 && g->ws > 0 && g->cp > 0 &&
            g->kf > 0 && g->lp > 0 && g->le > 0 && g->rc2 > 0 && g->lp1 > 0;
   }
 };
@@ -472,13 +478,53 @@ void enqueue_sort(const Ctx& c, const Layout& lay, const Grids& g, uint32_t narr
   hook(PK_COPY, st, [&] { T::copy<<<min_u32(lay.copytilecap, (uint32_t)g.cp), T::SNT, 0, st>>>(c); });
 }
 
+// Whether a call runs as one persistent launch (dfr_persist.cuh): the plan's
+// launch form (DFR_LAUNCH_*), the MSD schedule only, and a device on which
+// the persistent kernel fits (g.ps > 0).
+inline bool use_persist(const dfr_tune_t& t, uint64_t ntot, uint32_t lsd_mode, const Grids& g, bool persist_ok) {
+  if (!persist_ok || lsd_mode != 0u || g.ps <= 0 || t.launch == DFR_LAUNCH_LEVELS) return false;
+  return t.launch == DFR_LAUNCH_PERSISTENT || ntot < DFR_PERSIST_AUTO_KEYS;
+}
+
+// The persistent launch of one call: the control block and the per-array
+// root accumulators are zeroed by a memset (the grid barrier's counters live
+// in the control block), then one cooperative launch runs every phase.  Its
+// grid: one CTA per 2048 keys and per array, at most what is resident at
+// once (g.ps).  Returns the first CUDA error.
+template <class K, class V, int G, class Hook>
+cudaError_t enqueue_persist(const Ctx& c, const Layout& lay, const Grids& g, uint32_t narr, uint32_t root_tiles,
+                            unsigned long long ntot, const ArrDesc& a0, bool write_a0, int fmt, cudaStream_t st,
+                            Hook&& hook) {
+  using T = Kernels<K, V, G>;
+  const size_t zero_bytes = lay.root + (size_t)narr * sizeof(RootAcc<K>) - lay.ctl;
+  const uint64_t want = ntot / 2048u + narr;
+  const uint32_t grid = (uint32_t)std::max<uint64_t>(1u, std::min<uint64_t>(want, (uint64_t)g.ps));
+  cudaError_t e = cudaSuccess;
+  hook(PK_PERSIST, st, [&] {
+    e = cudaMemsetAsync(c.ctl, 0, zero_bytes, st);
+    if (e != cudaSuccess) return;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(T::PC::NT);
+    cfg.dynamicSmemBytes = T::PC::smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, T::persist, c, a0, write_a0 ? 1u : 0u, root_tiles, ntot, (uint32_t)fmt);
+  });
+  return e;
+}
+
 // Regular entry: checks, layout, descriptor table, then enqueue_sort with
 // profiling hooks.  `batch` = the descriptor table is uploaded with one copy
 // (else the single descriptor rides in k_init's parameters, keeping the call
 // a pure kernel sequence).
 template <class K, class V, int G>
 int run_sort_g(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws_bytes, cudaStream_t st,
-               int fmt) {
+               int fmt, bool persist_ok) {
   using T = Kernels<K, V, G>;
   if (!fmt_valid(fmt)) return DFR_ERR_INVALID_ARG;
   if (narr == 0) return DFR_OK;
@@ -523,6 +569,12 @@ int run_sort_g(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t 
     rt_prof_end(PK_H2D, st);
     if (e != cudaSuccess) return DFR_ERR_CUDA;
   }
+  if (use_persist(tune, ntot, c.lsd_mode, g, persist_ok)) {
+    if (enqueue_persist<K, V, G>(c, lay, g, narr, rt, (unsigned long long)ntot, tab[0], !batch, fmt, st, hook) !=
+        cudaSuccess)
+      return DFR_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? DFR_OK : DFR_ERR_CUDA;
+  }
   // Signed, float or descending keys: map every key to its unsigned image in
   // place, sort the images, map them back (two extra read+write passes).
   const uint32_t kf_grid = min_u32(rt, (uint32_t)g.kf);
@@ -537,11 +589,11 @@ int run_sort_g(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t 
 // A call in the geometry its array sizes select (geometry_of).
 template <class K, class V>
 int run_sort(const HostArr* arrs, uint32_t narr, bool batch, void* ws, size_t ws_bytes, cudaStream_t st,
-             int fmt = DFR_FMT_UNSIGNED) {
+             int fmt = DFR_FMT_UNSIGNED, bool persist_ok = true) {
   uint64_t ntot = 0;  // (each n is validated by run_sort_g)
   for (uint32_t a = 0; a < narr; ++a) ntot += arrs[a].n;
-  return geometry_of<K, V>(ntot, narr) ? run_sort_g<K, V, 1>(arrs, narr, batch, ws, ws_bytes, st, fmt)
-                                       : run_sort_g<K, V, 0>(arrs, narr, batch, ws, ws_bytes, st, fmt);
+  return geometry_of<K, V>(ntot, narr) ? run_sort_g<K, V, 1>(arrs, narr, batch, ws, ws_bytes, st, fmt, persist_ok)
+                                       : run_sort_g<K, V, 0>(arrs, narr, batch, ws, ws_bytes, st, fmt, persist_ok);
 }
 
 // Capture one call's launch sequence into an executable CUDA graph bound to
@@ -581,22 +633,37 @@ int build_graph_g(const HostArr* arrs, uint32_t narr, void* ws, size_t ws_bytes,
     return DFR_ERR_CUDA;
   cudaStream_t cs = nullptr;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return DFR_ERR_CUDA;
-  rc = DFR_OK;
-  cudaGraph_t graph = nullptr;
-  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    rc = DFR_ERR_CUDA;
-  } else {
+  // Capture the persistent launch where the plan picks it; should that
+  // capture fail, capture the level sequence instead.
+  auto capture = [&](bool persist) -> int {
+    cudaGraph_t graph = nullptr;
+    int r = DFR_OK;
     uint32_t n = 0;
-    enqueue_sort<K, V, G>(c, lay, g, narr, rt, (unsigned long long)ntot, tab[0], false, cs,
-                       [&n](int, cudaStream_t, auto&& fn) {
-                         fn();
-                         ++n;
-                       });
-    if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || !graph) rc = DFR_ERR_CUDA;
-    if (rc == DFR_OK && cudaGraphInstantiate(out, graph, 0) != cudaSuccess) rc = DFR_ERR_CUDA;
+    auto count = [&n](int, cudaStream_t, auto&& fn) {
+      fn();
+      ++n;
+    };
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DFR_ERR_CUDA;
+    if (persist) {
+      if (enqueue_persist<K, V, G>(c, lay, g, narr, rt, (unsigned long long)ntot, tab[0], false, DFR_FMT_UNSIGNED,
+                                   cs, count) != cudaSuccess)
+        r = DFR_ERR_CUDA;
+    } else {
+      enqueue_sort<K, V, G>(c, lay, g, narr, rt, (unsigned long long)ntot, tab[0], false, cs, count);
+    }
+    if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || !graph) r = DFR_ERR_CUDA;
+    if (r == DFR_OK && cudaGraphInstantiate(out, graph, 0) != cudaSuccess) r = DFR_ERR_CUDA;
+    if (graph) cudaGraphDestroy(graph);
+    if (r != DFR_OK) {
+      *out = nullptr;
+      cudaGetLastError();  // clear the failed capture's error before a retry
+    }
     *nodes = n;
-  }
-  if (graph) cudaGraphDestroy(graph);
+    return r;
+  };
+  const bool persist = use_persist(tune, ntot, c.lsd_mode, g, true);
+  rc = capture(persist);
+  if (rc != DFR_OK && persist) rc = capture(false);
   cudaStreamDestroy(cs);
   if (rc != DFR_OK) *out = nullptr;
   return rc;
@@ -612,12 +679,18 @@ int build_graph(const HostArr* arrs, uint32_t narr, void* ws, size_t ws_bytes, c
 }
 
 // Entry points instantiated per key type (dfr_u32.cu, ...).
-int run_u32(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
-int run_u32_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
-int run_u64(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
-int run_u64_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
-int run_u64_kv64(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
-int run_u32_kv64(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt);
+int run_u32(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt,
+            bool persist_ok);
+int run_u32_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt,
+            bool persist_ok);
+int run_u64(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt,
+            bool persist_ok);
+int run_u64_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt,
+            bool persist_ok);
+int run_u64_kv64(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt,
+            bool persist_ok);
+int run_u32_kv64(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt,
+            bool persist_ok);
 size_t ws_u32(uint64_t ntot, uint32_t narr);
 size_t ws_u32_kv(uint64_t ntot, uint32_t narr);
 size_t ws_u64(uint64_t ntot, uint32_t narr);
@@ -632,7 +705,7 @@ int graph_u64_kv64(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraph
 int graph_u32_kv64(const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out, uint32_t* nodes);
 // Dispatch by key type, and the device error word as a DFR status (dfr_api.cu).
 int run_typed(int key_type, const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st,
-              int fmt = DFR_FMT_UNSIGNED);
+              int fmt = DFR_FMT_UNSIGNED, bool persist_ok = true);
 int graph_typed(int key_type, const HostArr* a, uint32_t n, void* ws, size_t wsb, cudaGraphExec_t* out,
                 uint32_t* nodes);
 int ws_typed(int key_type, uint64_t ntot, uint32_t narr, size_t* bytes);

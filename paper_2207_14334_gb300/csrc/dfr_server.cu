@@ -247,7 +247,10 @@ void dfr_server::launch(Batch* b, std::vector<dfr_segment_t>& segs) {
     std::vector<HostArr> arrs(segs.size());
     for (size_t i = 0; i < segs.size(); ++i)
       arrs[i] = HostArr{segs[i].keys, segs[i].kbuf, segs[i].vals, segs[i].vbuf, segs[i].n};
-    rc = run_typed(segs[0].key_type, arrs.data(), (uint32_t)arrs.size(), arrs.size() > 1, ws, b->bytes, st);
+    // the level sequence: batches on several streams run side by side,
+    // which a cooperative launch's whole-grid residency would serialise
+    rc = run_typed(segs[0].key_type, arrs.data(), (uint32_t)arrs.size(), arrs.size() > 1, ws, b->bytes, st,
+                   DFR_FMT_UNSIGNED, false);
   }
   bool any = false;
   for (const auto& g : segs) any = any || g.n > 1;

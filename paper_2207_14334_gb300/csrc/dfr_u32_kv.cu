@@ -3,8 +3,8 @@
 
 namespace dfr {
 
-int run_u32_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt) {
-  return run_sort<uint32_t, uint32_t>(a, n, batch, ws, wsb, st, fmt);
+int run_u32_kv(const HostArr* a, uint32_t n, bool batch, void* ws, size_t wsb, cudaStream_t st, int fmt, bool persist_ok) {
+  return run_sort<uint32_t, uint32_t>(a, n, batch, ws, wsb, st, fmt, persist_ok);
 }
 
 size_t ws_u32_kv(uint64_t ntot, uint32_t narr) { return workspace_bytes<uint32_t, uint32_t>(ntot, narr); }

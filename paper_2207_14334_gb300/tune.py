@@ -30,7 +30,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 INC = os.path.join(HERE, "csrc", "dfr_tune_table.inc")
 
 KEY_TYPES = ("DFR_U32", "DFR_U64", "DFR_U64_KV", "DFR_U32_KV", "DFR_U64_KV64", "DFR_U32_KV64")  # row order of the C table
-FIELDS = ("target_log2", "max_bits", "warp_max", "scatter_ctas_per_sm", "ctasort_ctas_per_sm", "schedule")
+FIELDS = ("target_log2", "max_bits", "warp_max", "scatter_ctas_per_sm", "ctasort_ctas_per_sm", "schedule", "launch")
 
 
 def class_length(c: int) -> int:
@@ -143,12 +143,13 @@ def tune(key_types, classes, reps: int, budget_keys: int, schedules=(0, 1), log=
 
 
 def write_inc(table, path=INC, note=""):
-    default = dict(target_log2=12, max_bits=8, warp_max=512, scatter_ctas_per_sm=0, ctasort_ctas_per_sm=0, schedule=0)
+    default = dict(target_log2=12, max_bits=8, warp_max=512, scatter_ctas_per_sm=0, ctasort_ctas_per_sm=0, schedule=0,
+                   launch=0)
     lines = ["// dfr_tune_table.inc -- the built-in launch plans, one row per key type",
              "// (" + ", ".join(KEY_TYPES) + ")",
              "// and size class (mean array",
              "// length 2^<12, [2^12, 2^14), ..., 2^28+).  Fields: target_log2, max_bits,",
-             "// warp_max, scatter_ctas_per_sm, ctasort_ctas_per_sm, schedule, reserved x2.",
+             "// warp_max, scatter_ctas_per_sm, ctasort_ctas_per_sm, schedule, launch, reserved.",
              "// Written by paper_2207_14334_gb300/tune.py" + (": " + note if note else "") + "."]
     for ktn in KEY_TYPES:
         rows = []
@@ -156,7 +157,7 @@ def write_inc(table, path=INC, note=""):
             e = table.get(ktn, {}).get(str(c))
             if e is None:
                 e = dict(default, target_log2=12 if ktn == "DFR_U32" else 11)
-            rows.append("{%d, %d, %d, %d, %d, %d, {0, 0}}" % tuple(int(e.get(f, 0)) for f in FIELDS))
+            rows.append("{%d, %d, %d, %d, %d, %d, %d, 0}" % tuple(int(e.get(f, 0)) for f in FIELDS))
         body = ",\n ".join(", ".join(rows[i:i + 3]) for i in range(0, 10, 3))
         lines.append("{" + body + "},")
     with open(path, "w") as f:

@@ -122,12 +122,12 @@ def test_tune_table_api(lib):
     base = dfr.dfr_tune_get(dfr.DFR_U32, 3)
     try:
         new = dict(base, target_log2=9, max_bits=6, warp_max=256, scatter_ctas_per_sm=1, ctasort_ctas_per_sm=1,
-                   schedule=dfr.DFR_SCHED_DFR)
+                   schedule=dfr.DFR_SCHED_DFR, launch=dfr.DFR_LAUNCH_PERSISTENT)
         assert dfr.dfr_tune_set(dfr.DFR_U32, 3, new) == dfr.DFR_OK
         assert dfr.dfr_tune_get(dfr.DFR_U32, 3) == new
         for bad in (dict(base, target_log2=5), dict(base, target_log2=14), dict(base, max_bits=3),
                     dict(base, max_bits=9), dict(base, warp_max=64), dict(base, warp_max=1024),
-                    dict(base, scatter_ctas_per_sm=5), dict(base, schedule=3)):
+                    dict(base, scatter_ctas_per_sm=5), dict(base, schedule=3), dict(base, launch=3)):
             assert dfr.dfr_tune_set(dfr.DFR_U32, 3, bad) == dfr.DFR_ERR_INVALID_ARG
         assert dfr.dfr_tune_set(7, 3, base) == dfr.DFR_ERR_INVALID_ARG
         assert dfr.dfr_tune_set(dfr.DFR_U32, dfr.DFR_TUNE_CLASSES, base) == dfr.DFR_ERR_INVALID_ARG
@@ -144,16 +144,20 @@ def test_tuner_writes_a_table_the_library_compiles(tmp_path):
     table = {"DFR_U32": {"3": dict(target_log2=11, max_bits=7, warp_max=256, scatter_ctas_per_sm=2,
                                    ctasort_ctas_per_sm=1),
                          "9": dict(target_log2=12, max_bits=8, warp_max=512, scatter_ctas_per_sm=0,
-                                   ctasort_ctas_per_sm=0, schedule=2)}}
+                                   ctasort_ctas_per_sm=0, schedule=2),
+                         "0": dict(target_log2=11, max_bits=8, warp_max=512, scatter_ctas_per_sm=0,
+                                   ctasort_ctas_per_sm=0, launch=1)}}
     p = tmp_path / "t.inc"
     tune.write_inc(table, path=str(p), note="test")
     body = "".join(l for l in p.read_text().splitlines(True) if not l.startswith("//"))
     assert len(tune.KEY_TYPES) == 6
-    assert body.count("{0, 0}}") == len(tune.KEY_TYPES) * dfr.DFR_TUNE_CLASSES
-    assert "{11, 7, 256, 2, 1, 0, {0, 0}}" in body
-    assert "{12, 8, 512, 0, 0, 2, {0, 0}}" in body
-    shipped = open(tune.INC).read()
-    assert "".join(l for l in shipped.splitlines(True) if not l.startswith("//")).count("{0, 0}}") == \
+    rows = re.findall(r"\{(\d+), (\d+), (\d+), (\d+), (\d+), (\d+), (\d+), 0\}", body)
+    assert len(rows) == len(tune.KEY_TYPES) * dfr.DFR_TUNE_CLASSES  # eight fields per entry, reserved zero
+    assert "{11, 7, 256, 2, 1, 0, 0, 0}" in body
+    assert "{12, 8, 512, 0, 0, 2, 0, 0}" in body
+    assert "{11, 8, 512, 0, 0, 0, 1, 0}" in body
+    shipped = "".join(l for l in open(tune.INC).read().splitlines(True) if not l.startswith("//"))
+    assert len(re.findall(r"\{(\d+), (\d+), (\d+), (\d+), (\d+), (\d+), (\d+), 0\}", shipped)) == \
         len(tune.KEY_TYPES) * dfr.DFR_TUNE_CLASSES
 
 
@@ -180,7 +184,7 @@ def test_key_format_host_checks(lib):
     # n <= 1 is a no-op in every format
     assert dfr.dfr_sort_format(dfr.DFR_U64, dfr.DFR_FMT_SIGNED, 0x1000, 0, 0x2000, 0, 1, 0, 0, stream=0) == dfr.DFR_OK
     names = [lib.dfr_profile_kind_name(i) for i in range(dfr.DFR_PROFILE_KINDS)]
-    assert names[-3:] == [b"keyfmt", b"lsd_pass", b"lsd_plan"]
+    assert names[-4:] == [b"keyfmt", b"lsd_pass", b"lsd_plan", b"persist"]
 
 
 def test_workspace_bytes_never_decrease(lib):
