@@ -137,6 +137,8 @@ struct LevelCtl {
   uint32_t ntiles;
   uint32_t hist_claim;
   uint32_t scat_claim;
+  uint32_t ncnt;  // segments that need the level count (histogram or AND/OR)
+  uint32_t pad;
   unsigned long long keys;       // keys dealt at this level
   unsigned long long hist_keys;  // keys read by k_level_count
 };
@@ -668,6 +670,45 @@ __device__ __forceinline__ void atomic_or_key(K* p, K v) {
     atomicOr(reinterpret_cast<uint32_t*>(p), (uint32_t)v);
 }
 
+// End of a warp-granular count (root and level counts): the warps of the CTA
+// that ended on the same target (an array or a segment) merge their private
+// counters and OR / NOT-AND registers, and one warp per target adds the sums
+// to the target -- one global atomic per bin and CTA instead of per warp.
+// add_hist(target, bin, count), add_ornand(target, or, not_and).  Every
+// thread of the block calls it; s_h holds the NW warps' M counters each.
+template <class K, int NW, class AddHist, class AddOrNand>
+__device__ __forceinline__ void cta_merge_counts(const uint32_t* s_h, uint32_t cur, K orv, K nandv,
+                                                 AddHist&& add_hist, AddOrNand&& add_ornand) {
+  __shared__ uint32_t s_wcur[NW];
+  __shared__ K s_wor[NW], s_wnand[NW];
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const K o = warp_or(orv), na = warp_or(nandv);
+  if (lane == 0) {
+    s_wcur[warp] = cur;
+    s_wor[warp] = o;
+    s_wnand[warp] = na;
+  }
+  __syncthreads();
+  if (cur == 0xffffffffu) return;
+  for (uint32_t w = 0; w < warp; ++w)
+    if (s_wcur[w] == cur) return;  // an earlier warp leads this target
+  K mo = 0, mna = 0;
+  for (uint32_t w = warp; w < (uint32_t)NW; ++w)
+    if (s_wcur[w] == cur) {
+      mo |= s_wor[w];
+      mna |= s_wnand[w];
+    }
+#pragma unroll
+  for (int i = 0; i < M / 32; ++i) {
+    const uint32_t bin = (uint32_t)i * 32u + lane;
+    uint32_t sum = 0;
+    for (uint32_t w = warp; w < (uint32_t)NW; ++w)
+      if (s_wcur[w] == cur) sum += s_h[w * M + bin];
+    if (sum) add_hist(cur, bin, sum);
+  }
+  if (lane == 0) add_ornand(cur, mo, mna);
+}
+
 // Root count: one read of every key; per array the OR / NOT-AND of its keys
 // and the histogram of its top byte (the initial counting pass, Alg. 1).
 // Every warp claims whole tiles on its own and keeps private counters and
@@ -679,7 +720,7 @@ __device__ __forceinline__ void atomic_or_key(K* p, K v) {
 // nothing.
 template <class K, int NT, int TILE, bool TWO>
 __device__ __forceinline__ void root_count_body(const Ctx& c, uint32_t root_tiles, uint32_t* h2, uint32_t* s_h,
-                                                uint32_t* s_h2) {
+                                                uint32_t* s_h2, uint32_t sub = 1u) {
   constexpr uint32_t TOP = 8 * sizeof(K) - RB;
   if (c.lsd_mode == 2u && ld_relaxed(&c.lsd->on) != 0u) {
     if (blockIdx.x == 0 && threadIdx.x == 0) c.ctl->root_skipped = 1u;
@@ -709,11 +750,15 @@ __device__ __forceinline__ void root_count_body(const Ctx& c, uint32_t root_tile
     orv = 0;
     nandv = 0;
   };
+  // a warp claims 1/sub of a tile at a time (sub > 1 spreads a small call's
+  // few tiles over more warps)
+  const uint32_t part_keys = (uint32_t)TILE / sub;
   for (;;) {
-    uint32_t t = 0;
-    if (lane == 0) t = atomicAdd(&c.ctl->root_claim, 1u);
-    t = __shfl_sync(FULL, t, 0);
-    if (t >= root_tiles) break;
+    uint32_t u = 0;
+    if (lane == 0) u = atomicAdd(&c.ctl->root_claim, 1u);
+    u = __shfl_sync(FULL, u, 0);
+    if (u >= root_tiles * sub) break;
+    const uint32_t t = u / sub, part = u - t * sub;
     uint32_t lo = 0, hi = c.narr - 1;
     while (lo < hi) {
       const uint32_t mid = (lo + hi + 1) >> 1;
@@ -728,11 +773,21 @@ __device__ __forceinline__ void root_count_body(const Ctx& c, uint32_t root_tile
     }
     const ArrDesc ad = c.arrs[lo];
     const uint32_t j = t - ad.root_tile_start;
-    const uint32_t b = j * (uint32_t)TILE;
-    const uint32_t e = min(ad.n, b + (uint32_t)TILE);
-    warp_count_range<K, TWO>(reinterpret_cast<const K*>(ad.keys), b, e, TOP, true, wh, orv, nandv, wh2, TOP - RB);
+    const uint32_t b = j * (uint32_t)TILE + part * part_keys;
+    const uint32_t e = min(ad.n, b + part_keys);
+    if (b < e)
+      warp_count_range<K, TWO>(reinterpret_cast<const K*>(ad.keys), b, e, TOP, true, wh, orv, nandv, wh2, TOP - RB);
   }
-  flush();
+  if constexpr (TWO) {
+    flush();
+  } else {
+    cta_merge_counts<K, NT / 32>(
+        s_h, cur, orv, nandv, [&](uint32_t a, uint32_t bin, uint32_t v) { atomicAdd(&root[a].hist[bin], v); },
+        [&](uint32_t a, K o, K na) {
+          atomic_or_key(&root[a].orv, o);
+          atomic_or_key(&root[a].nand, na);
+        });
+  }
 }
 
 template <class K, int NT, int TILE, bool TWO>
@@ -875,6 +930,7 @@ __device__ __forceinline__ void root_classify_body(const Ctx& c, unsigned long l
       if (s_ok) {
         c.segs[0][s] = Seg{0u, n, a, ts, shift, 0u, use_top ? 0u : SEG_NEEDS_HIST, bits,
                            (unsigned long long)root[a].nand, (unsigned long long)orv};
+        if (!use_top) atomicAdd(&ctl->lv[0].ncnt, 1u);
       } else {
         // Cannot happen with the workspace bounds; stay consistent anyway.
         atomicOr(&ctl->err, DERR_CAPACITY);
@@ -919,7 +975,7 @@ __global__ void __launch_bounds__(256) k_root_classify(Ctx c, unsigned long long
 // of the level.  Warp-granular like k_root_count: private counters flushed per
 // segment.
 template <class K, bool KV, int NT, int TILE>
-__device__ __forceinline__ void level_count_body(const Ctx& c, int L, uint32_t* s_h) {
+__device__ __forceinline__ void level_count_body(const Ctx& c, int L, uint32_t* s_h, uint32_t sub = 1u) {
   LevelCtl* lc = &c.ctl->lv[L];
   const uint32_t ntiles = min(lc->ntiles, c.tilecap);
   Seg* segs = ((L & 1) ? c.segs[1] : c.segs[0]);
@@ -945,14 +1001,19 @@ __device__ __forceinline__ void level_count_body(const Ctx& c, int L, uint32_t* 
     orv = 0;
     nandv = 0;
   };
+  // a warp claims 1/sub of a tile at a time (as in the root count)
+  const uint32_t part_keys = (uint32_t)TILE / sub;
   for (;;) {
-    uint32_t t = 0;
-    if (lane == 0) t = atomicAdd(&lc->hist_claim, 1u);
-    t = __shfl_sync(FULL, t, 0);
-    if (t >= ntiles) break;
+    uint32_t u = 0;
+    if (lane == 0) u = atomicAdd(&lc->hist_claim, 1u);
+    u = __shfl_sync(FULL, u, 0);
+    if (u >= ntiles * sub) break;
+    const uint32_t t = u / sub, part = u - t * sub;
     if constexpr (KV) {
+      if (part == 0u) {
 #pragma unroll
-      for (int i = 0; i < M / 32; ++i) c.status[(size_t)t * M + i * 32 + lane] = 0u;
+        for (int i = 0; i < M / 32; ++i) c.status[(size_t)t * M + i * 32 + lane] = 0u;
+      }
     }
     const uint32_t s = c.tile_owner[t];
     if (s >= c.segcap) continue;
@@ -967,13 +1028,24 @@ __device__ __forceinline__ void level_count_body(const Ctx& c, int L, uint32_t* 
     const uint32_t j = t - seg.tile_start;
     const ArrDesc ad = c.arrs[seg.arr];
     const K* src = reinterpret_cast<const K*>(seg.parity ? ad.buf : ad.keys);
-    const uint32_t tb = tile_base<K>(seg.off) + j * (uint32_t)TILE;
-    const uint32_t b = max(tb, seg.off);
-    const uint32_t e = min(seg.off + seg.len, tb + (uint32_t)TILE);
+    const uint32_t pb = tile_base<K>(seg.off) + j * (uint32_t)TILE + part * part_keys;
+    const uint32_t b = max(pb, seg.off);
+    const uint32_t e = min(seg.off + seg.len, pb + part_keys);
+    if (b >= e) continue;
     warp_count_range<K>(src, b, e, seg.shift, (flags & SEG_NEEDS_HIST) != 0u, wh, orv, nandv);
     keys_read += e - b;
   }
-  flush();
+  cta_merge_counts<K, NT / 32>(
+      s_h, cur, orv, nandv,
+      [&](uint32_t sg, uint32_t bin, uint32_t v) {
+        if (cur_flags & SEG_NEEDS_HIST) atomicAdd(&hist[(size_t)sg * M + bin], v);
+      },
+      [&](uint32_t sg, K o, K na) {
+        if (cur_flags & SEG_NEEDS_ANDOR) {
+          atomic_or_u64(&segs[sg].orv, (unsigned long long)o);
+          atomic_or_u64(&segs[sg].nand, (unsigned long long)na);
+        }
+      });
   if (lane == 0 && keys_read) atomicAdd(&lc->hist_keys, keys_read);
 }
 
@@ -1373,6 +1445,123 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, false, NT>()))
   scatter_body<K, V, NT, KPT>(c, L);
 }
 
+// Inclusive scan with an associative `op` over threads [0, 256), forward
+// (thread x gets op(v_0 .. v_x)) or, with REV, backward (op(v_x .. v_255));
+// threads >= 256 contribute `ident`.  Every thread of the block calls it (two
+// barriers); `sh` holds 8 words.
+template <bool REV, class Op>
+__device__ __forceinline__ uint32_t scan256_op(uint32_t v, uint32_t ident, Op op, uint32_t* sh) {
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+  uint32_t x = threadIdx.x < 256 ? v : ident;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = REV ? __shfl_down_sync(FULL, x, o) : __shfl_up_sync(FULL, x, o);
+    if (REV ? lane + (uint32_t)o < 32u : lane >= (uint32_t)o) x = op(x, y);
+  }
+  if (w < 8 && lane == (REV ? 0u : 31u)) sh[w] = x;
+  __syncthreads();
+  uint32_t acc = ident;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    if (REV ? i > (int)w : i < (int)w) acc = op(acc, sh[i]);
+  __syncthreads();
+  return op(acc, x);
+}
+
+// Bulk diversion of the small buckets of one segment (Section "Diverting
+// Fast Radix": small buckets are sorted together): consecutive small buckets,
+// in digit order, are packed greedily into runs of at most T keys -- a run
+// starts at a non-empty small bucket and takes the following buckets while
+// they fit, ends before a bucket that does not fit (which starts the next
+// run) or at a large bucket (the next run starts at the first non-empty small
+// bucket after it).  Computed in parallel with one thread per digit: f(x),
+// the start of the run after a run that starts at x, comes from prefix sums
+// (a binary search for the first bucket that does not fit) and two suffix
+// scans; the run starts are the chain x0, f(x0), f(f(x0)), ..., found by
+// pointer jumping (8 doublings for 256 digits).  The runs are the ones a
+// serial greedy walk gives, written in digit order: offset, length and the
+// bound on the run's highest varying bit + 1 (digits of the run that differ
+// vary in the window).  cnt[x] = bucket size, LARGE for a large bucket.
+// Every thread of the block calls it; `tmp` holds 4 x 256 words.
+template <uint32_t T>
+__device__ __forceinline__ uint32_t pack_runs(const uint32_t* cnt, const uint32_t* boff, uint32_t shift,
+                                              uint32_t* run_off, uint32_t* run_len, uint32_t* run_top,
+                                              uint32_t* tmp, uint32_t* sh) {
+  constexpr uint32_t LARGE = 0xffffffffu, END = 256u;
+  const uint32_t x = threadIdx.x;
+  const bool dig = x < 256u;
+  const uint32_t cx = dig ? cnt[x] : 0u;
+  const bool large = dig && cx == LARGE, start_ok = dig && cx != LARGE && cx != 0u;
+  const uint32_t v = (dig && !large) ? cx : 0u;
+  uint32_t* P = tmp;          // inclusive prefix sums of the small buckets
+  uint32_t* NL = tmp + 256;   // first large bucket >= x (END if none)
+  uint32_t* NS = tmp + 512;   // first non-empty small bucket >= x
+  uint32_t* PS = tmp + 768;   // last non-empty small bucket <= x, plus one (0 if none)
+  auto plus = [](uint32_t a, uint32_t b) { return a + b; };
+  auto mn = [](uint32_t a, uint32_t b) { return a < b ? a : b; };
+  auto mx = [](uint32_t a, uint32_t b) { return a > b ? a : b; };
+  const uint32_t pin = scan256_op<false>(v, 0u, plus, sh);
+  const uint32_t nl = scan256_op<true>(large ? x : END, END, mn, sh);
+  const uint32_t ns = scan256_op<true>(start_ok ? x : END, END, mn, sh);
+  const uint32_t ps = scan256_op<false>(start_ok ? x + 1u : 0u, 0u, mx, sh);
+  if (dig) {
+    P[x] = pin;
+    NL[x] = nl;
+    NS[x] = ns;
+    PS[x] = ps;
+  }
+  __syncthreads();
+  // a run starting at x: it stops at y (the first bucket after x that is
+  // large or no longer fits), and the next run starts at nxt
+  uint32_t y = END, nxt = END, rlen = 0, last = 0;
+  if (start_ok) {
+    const uint32_t lim = pin - v + T;  // prefix sum up to which the run's buckets fit
+    uint32_t lo = x + 1u, hi = END;    // first z in [x+1, END) with P[z] > lim, else END
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (P[mid] > lim)
+        hi = mid;
+      else
+        lo = mid + 1u;
+    }
+    const uint32_t lg = x + 1u < END ? NL[x + 1u] : END;
+    y = lo < lg ? lo : lg;
+    nxt = y == END ? END : (y == lg ? (y + 1u < END ? NS[y + 1u] : END) : y);
+    rlen = P[y - 1u] - (pin - v);  // the small buckets in [x, y)
+    last = PS[y - 1u] - 1u;        // the run's last non-empty bucket
+  }
+  // pointer jumping: after round k every run start within 2^(k+1) steps of
+  // the first one is marked
+  uint32_t* J = tmp;         // (reuses P: read above, before this barrier)
+  uint32_t* MK = tmp + 512;  // (reuses NS)
+  const uint32_t x0 = NS[0];
+  __syncthreads();
+  if (dig) {
+    J[x] = nxt;
+    MK[x] = (x == x0) ? 1u : 0u;
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) {
+    uint32_t j = dig ? J[x] : END;
+    if (dig && MK[x] && j < END) MK[j] = 1u;
+    const uint32_t jj = (dig && j < END) ? J[j] : END;
+    __syncthreads();
+    if (dig) J[x] = jj;
+    __syncthreads();
+  }
+  const bool is_start = dig && MK[x] != 0u;
+  uint32_t nrun = 0;
+  const uint32_t idx = scan256(is_start ? 1u : 0u, sh, &nrun);
+  if (is_start) {
+    run_off[idx] = boff[x];
+    run_len[idx] = rlen;
+    run_top[idx] = shift + (x == last ? 0u : 32u - (uint32_t)__clz((int)(x ^ last)));
+  }
+  __syncthreads();
+  return nrun;
+}
+
 // Classification of one level, one CTA (256 threads = one per digit) per
 // segment.  A constant segment is finished (copied back if it sits in the
 // buffer); a segment whose window held no varying bit is passed to the next
@@ -1389,10 +1578,14 @@ __device__ __forceinline__ void classify_body(const Ctx& c, int L) {
   // New next-level segments / large copy items of this segment: owner value
   // for their tile range, histogram slot to clear, first tile, tile count.
   __shared__ uint32_t s_new_owner[M], s_new_zero[M], s_new_ts[M], s_new_nt[M], s_new_copy[M];
-  __shared__ unsigned long long s_stat[10];
-  __shared__ uint32_t s_bcnt[M], s_boff[M], s_run_off[M], s_run_len[M];
+  // per-segment statistics (every count fits 32 bits: a segment holds < 2^30
+  // keys); native 32-bit shared atomics, added to the 64-bit totals once
+  __shared__ uint32_t s_stat[10];
+  __shared__ __align__(16) uint32_t s_bcnt[M];
+  __shared__ uint32_t s_boff[M], s_run_off[M], s_run_len[M];
   __shared__ uint32_t s_nrun, s_qn[3], s_qbase[3];
   __shared__ uint32_t s_run_top[M];  // bound on each run's highest varying bit + 1
+  __shared__ uint32_t s_pack[4 * M];  // pack_runs' prefix sums, suffix scans and jump pointers
   Ctl* ctl = c.ctl;
   const uint32_t nseg = min(ctl->lv[L].nseg, c.segcap);
   const Seg* segs = ((L & 1) ? c.segs[1] : c.segs[0]);
@@ -1415,6 +1608,7 @@ __device__ __forceinline__ void classify_body(const Ctx& c, int L) {
     const bool ok = L + 1 < MAXLV && s2 < c.segcap && ts + nt <= c.tilecap;
     if (ok) {
       segs_n[s2] = Seg{off, cnt, arr, ts, shift, parity, flags, bits, nand, orv};
+      if (flags & (SEG_NEEDS_HIST | SEG_NEEDS_ANDOR)) atomicAdd(&ln->ncnt, 1u);
     } else {
       // Cannot happen with the workspace bounds; keep every slot consistent
       // anyway: an empty segment and tiles nobody processes.
@@ -1452,7 +1646,7 @@ __device__ __forceinline__ void classify_body(const Ctx& c, int L) {
       s_tiny_n = 0;
       s_new_n = 0;
     }
-    if (threadIdx.x < 10) s_stat[threadIdx.x] = 0ull;
+    if (threadIdx.x < 10) s_stat[threadIdx.x] = 0u;
     __syncthreads();
     const K vm = (K)seg.orv & (K)seg.nand;
     const bool dealt = vm != K(0) && ((vm >> seg.shift) & (K)(M - 1)) != K(0);
@@ -1460,7 +1654,7 @@ __device__ __forceinline__ void classify_body(const Ctx& c, int L) {
       if (threadIdx.x == 0 && seg.len > 0) {
         if (vm == K(0)) {
           // every key of the segment is equal: finished where it lies
-          s_stat[0] = 1ull;
+          s_stat[0] = 1u;
           s_stat[1] = seg.len;
           if (seg.parity) {
             s_stat[2] = seg.len;
@@ -1498,10 +1692,10 @@ __device__ __forceinline__ void classify_body(const Ctx& c, int L) {
         // they are constant and only move back if they sit in the buffer).
         if (cnt > (uint32_t)TCTA) {
           if (seg.shift == 0u) {
-            atomicAdd(&s_stat[0], 1ull);
-            atomicAdd(&s_stat[1], (unsigned long long)cnt);
+            atomicAdd(&s_stat[0], 1u);
+            atomicAdd(&s_stat[1], cnt);
             if (pout) {
-              atomicAdd(&s_stat[2], (unsigned long long)cnt);
+              atomicAdd(&s_stat[2], cnt);
               // the bucket's keys are the segment prefix with this digit
               const K val = (K)(((K)seg.orv & ~(((K)(M - 1)) << seg.shift)) | ((K)d << seg.shift));
               add_copy(off, cnt, seg.arr, (unsigned long long)val);
@@ -1522,36 +1716,15 @@ __device__ __forceinline__ void classify_body(const Ctx& c, int L) {
           s_boff[d] = off;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-          // (a run of one bucket varies below the window; one of several
-          // buckets also in the window bits where their digits differ)
-          uint32_t nr = 0, roff = 0, rlen = 0, dfirst = 0, dlast = 0;
-          auto close = [&]() {
-            s_run_off[nr] = roff;
-            s_run_len[nr] = rlen;
-            s_run_top[nr] = seg.shift + (dfirst == dlast ? 0u : 32u - (uint32_t)__clz((int)(dfirst ^ dlast)));
-            ++nr;
-          };
-          for (uint32_t x = 0; x < (uint32_t)M; ++x) {
-            const uint32_t cx = s_bcnt[x];
-            if (cx == 0u) continue;
-            if (cx == 0xffffffffu || rlen + cx > (uint32_t)TCTA) {
-              if (rlen) close();
-              rlen = 0;
-              if (cx == 0xffffffffu) continue;
-            }
-            if (rlen == 0) {
-              roff = s_boff[x];
-              dfirst = x;
-            }
-            dlast = x;
-            rlen += cx;
+        {
+          const uint32_t nr = pack_runs<(uint32_t)TCTA>(s_bcnt, s_boff, seg.shift, s_run_off, s_run_len, s_run_top,
+                                                        s_pack, s_scan);
+          if (threadIdx.x == 0) {
+            s_nrun = nr;
+            s_qn[0] = 0;
+            s_qn[1] = 0;
+            s_qn[2] = 0;
           }
-          if (rlen) close();
-          s_nrun = nr;
-          s_qn[0] = 0;
-          s_qn[1] = 0;
-          s_qn[2] = 0;
         }
         __syncthreads();
         const uint32_t nr = s_nrun;
@@ -1566,10 +1739,10 @@ __device__ __forceinline__ void classify_body(const Ctx& c, int L) {
             // repeated key (§MSD).  The run is final where it lies, or only
             // moves back from the buffer: the tiny pass copies up to a warp of
             // keys, a CTA-queue copy item the rest.
-            atomicAdd(&s_stat[0], 1ull);
-            atomicAdd(&s_stat[1], (unsigned long long)rlen);
+            atomicAdd(&s_stat[0], 1u);
+            atomicAdd(&s_stat[1], rlen);
             if (pout) {
-              atomicAdd(&s_stat[2], (unsigned long long)rlen);
+              atomicAdd(&s_stat[2], rlen);
               if (rlen <= T_WARP) {
                 rcls = 1;
               } else {
@@ -1579,28 +1752,28 @@ __device__ __forceinline__ void classify_body(const Ctx& c, int L) {
               }
             }
           } else if (rlen == 1u) {
-            atomicAdd(&s_stat[0], 1ull);
-            atomicAdd(&s_stat[1], 1ull);
+            atomicAdd(&s_stat[0], 1u);
+            atomicAdd(&s_stat[1], 1u);
             if (pout) {
-              atomicAdd(&s_stat[2], 1ull);
+              atomicAdd(&s_stat[2], 1u);
               rcls = 1;  // a single key in the buffer: copied by the tiny pass
             }
           } else if (rlen <= T_WARP) {
             rcls = 2;
-            atomicAdd(&s_stat[3], 1ull);
-            atomicAdd(&s_stat[4], (unsigned long long)rlen);
+            atomicAdd(&s_stat[3], 1u);
+            atomicAdd(&s_stat[4], rlen);
           } else if (rlen <= c.warp_max) {
             rcls = 3;
             rloc = atomicAdd(&s_qn[0], 1u);
-            atomicAdd(&s_stat[8], 1ull);
-            atomicAdd(&s_stat[7], (unsigned long long)rlen);
+            atomicAdd(&s_stat[8], 1u);
+            atomicAdd(&s_stat[7], rlen);
           } else {
             // a run whose keys may vary in more bits than k_ctasort32 sorts
             // goes to the general CTA sort's queue
             rcls = (two_cta_queues<K, V>() && s_run_top[threadIdx.x] > CTA32_SPAN) ? 5 : 4;
             rloc = atomicAdd(&s_qn[rcls - 3], 1u);
-            atomicAdd(&s_stat[5], 1ull);
-            atomicAdd(&s_stat[6], (unsigned long long)rlen);
+            atomicAdd(&s_stat[5], 1u);
+            atomicAdd(&s_stat[6], rlen);
           }
           if (rcls == 1 || rcls == 2) {
             const uint32_t i = atomicAdd(&s_tiny_n, 1u);
@@ -1609,10 +1782,10 @@ __device__ __forceinline__ void classify_body(const Ctx& c, int L) {
           }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-          s_qbase[0] = s_qn[0] ? atomicAdd(&ctl->wq_count, s_qn[0]) : 0u;
-          s_qbase[1] = s_qn[1] ? atomicAdd(&ctl->cta_count, s_qn[1]) : 0u;
-          s_qbase[2] = s_qn[2] ? atomicAdd(&ctl->cta2_count, s_qn[2]) : 0u;
+        if (threadIdx.x < 3u) {  // the three queues' slots, claimed side by side
+          const uint32_t qn = s_qn[threadIdx.x];
+          uint32_t* qc = threadIdx.x == 0u ? &ctl->wq_count : (threadIdx.x == 1u ? &ctl->cta_count : &ctl->cta2_count);
+          s_qbase[threadIdx.x] = qn ? atomicAdd(qc, qn) : 0u;
         }
         __syncthreads();
         if (rcls >= 3) {
@@ -1662,21 +1835,21 @@ __device__ __forceinline__ void classify_body(const Ctx& c, int L) {
     }
     if (threadIdx.x == 0) {
       if (s_stat[0]) {
-        atomicAdd(&ctl->const_buckets, s_stat[0]);
-        atomicAdd(&ctl->const_keys, s_stat[1]);
+        atomicAdd(&ctl->const_buckets, (unsigned long long)s_stat[0]);
+        atomicAdd(&ctl->const_keys, (unsigned long long)s_stat[1]);
       }
-      if (s_stat[2]) atomicAdd(&ctl->copy_keys, s_stat[2]);
+      if (s_stat[2]) atomicAdd(&ctl->copy_keys, (unsigned long long)s_stat[2]);
       if (s_stat[3]) {
-        atomicAdd(&ctl->tiny_buckets, s_stat[3]);
-        atomicAdd(&ctl->tiny_keys, s_stat[4]);
+        atomicAdd(&ctl->tiny_buckets, (unsigned long long)s_stat[3]);
+        atomicAdd(&ctl->tiny_keys, (unsigned long long)s_stat[4]);
       }
       if (s_stat[5]) {
-        atomicAdd(&ctl->cta_buckets, s_stat[5]);
-        atomicAdd(&ctl->cta_keys, s_stat[6]);
+        atomicAdd(&ctl->cta_buckets, (unsigned long long)s_stat[5]);
+        atomicAdd(&ctl->cta_keys, (unsigned long long)s_stat[6]);
       }
       if (s_stat[7]) {
-        atomicAdd(&ctl->wsort_keys, s_stat[7]);
-        atomicAdd(&ctl->wsort_buckets, s_stat[8]);
+        atomicAdd(&ctl->wsort_keys, (unsigned long long)s_stat[7]);
+        atomicAdd(&ctl->wsort_buckets, (unsigned long long)s_stat[8]);
       }
     }
     __syncthreads();
@@ -2074,6 +2247,7 @@ __device__ __forceinline__ void ctasort_body(const Ctx& c, int second) {
   __shared__ unsigned long long s_orv[2];
   Ctl* ctl = c.ctl;
   const uint32_t count = min(second ? ctl->cta2_count : ctl->cta_count, c.ctacap);
+  if (count == 0u) return;  // (the same value for every thread)
   uint32_t* claim = second ? &ctl->cta2_claim : &ctl->cta_claim;
   const Item* queue = second ? c.cta_q2 : c.cta_q;
 
@@ -2175,6 +2349,7 @@ __device__ __forceinline__ void warpsort_body(const Ctx& c) {
   uint32_t* wh = reinterpret_cast<uint32_t*>(sv + (KV ? WCAP : 0));
   Ctl* ctl = c.ctl;
   const uint32_t count = min(ctl->wq_count, c.wqcap);
+  if (count == 0u) return;
   for (;;) {
     uint32_t q = 0;
     if (lane == 0) q = atomicAdd(&ctl->wq_claim, 1u);
@@ -2340,6 +2515,7 @@ __device__ __forceinline__ void copy_body(const Ctx& c) {
   __shared__ uint32_t s_t;
   Ctl* ctl = c.ctl;
   const uint32_t ntiles = min(ctl->copy_tiles, c.copytilecap);
+  if (ntiles == 0u) return;  // (the same value for every thread)
   for (;;) {
     if (threadIdx.x == 0) s_t = atomicAdd(&ctl->copy_claim, 1u);
     __syncthreads();

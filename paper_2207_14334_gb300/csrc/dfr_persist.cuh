@@ -98,8 +98,16 @@ __global__ void __launch_bounds__(NT, 2)
   constexpr bool KV = !std::is_same<V, NoVal>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint32_t* s_h = reinterpret_cast<uint32_t*>(smem_raw);
-  __shared__ uint32_t s_ok;
+  __shared__ uint32_t s_ok, s_ntiles, s_ncnt;
   uint32_t gen = 0;
+  // Count phases: a warp claims 1/sub of a tile, sub (1..8, a power of two)
+  // chosen so that a call's tiles spread over the grid's warps.
+  auto sub_of = [&](uint32_t tiles) {
+    const uint32_t warps = gridDim.x * (uint32_t)(NT / 32);
+    uint32_t sub = 1u;
+    while (sub < 8u && tiles * sub * 2u <= warps) sub <<= 1;
+    return sub;
+  };
 
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (write_a0) c.arrs[0] = a0;
@@ -107,16 +115,28 @@ __global__ void __launch_bounds__(NT, 2)
   }
   if (fmt != DFR_FMT_UNSIGNED) keyfmt_body<K, P::NT, P::TILE>(c, a0, write_a0, root_tiles, fmt, 1u);
   if (!grid_sync(c, gen, &s_ok)) return;
-  root_count_body<K, P::NT, P::TILE, false>(c, root_tiles, nullptr, s_h, nullptr);
+  root_count_body<K, P::NT, P::TILE, false>(c, root_tiles, nullptr, s_h, nullptr, sub_of(root_tiles));
   if (!grid_sync(c, gen, &s_ok)) return;
   root_classify_body<K, V, P::TILE, P::TCTA, P::WCAP, P::NT>(c, n_total);
   if (!grid_sync(c, gen, &s_ok)) return;
   for (int L = 0; L < (int)c.nlev; ++L) {
     // the previous classification's last barrier published this level's
-    // segment count; every CTA reads the same value
-    if (ld_acquire_gpu(&c.ctl->lv[L].nseg) == 0u) break;
-    level_count_body<K, KV, P::NT, P::TILE>(c, L, s_h);
-    if (!grid_sync(c, gen, &s_ok)) return;
+    // segment and tile counts; every CTA reads the same values
+    if (threadIdx.x == 0) {
+      s_ntiles = ld_acquire_gpu(&c.ctl->lv[L].nseg) ? ld_acquire_gpu(&c.ctl->lv[L].ntiles) : 0u;
+      s_ncnt = ld_acquire_gpu(&c.ctl->lv[L].ncnt);
+    }
+    __syncthreads();
+    const uint32_t ntiles = s_ntiles;
+    if (ntiles == 0u) break;
+    // the count (and its barrier) only where a segment needs it: level 0
+    // segments whose window is the top byte already have the root count's
+    // histogram and AND/OR (key-value sorts always run it: it also clears
+    // the level's look-back words)
+    if (KV || s_ncnt != 0u) {
+      level_count_body<K, KV, P::NT, P::TILE>(c, L, s_h, sub_of(ntiles));
+      if (!grid_sync(c, gen, &s_ok)) return;
+    }
     scatter_body<K, V, NT, SKPT>(c, L);
     if (!grid_sync(c, gen, &s_ok)) return;
     classify_body<K, V, P::TILE, P::TCTA, P::WCAP, P::NT>(c, L);
