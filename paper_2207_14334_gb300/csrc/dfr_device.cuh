@@ -1135,10 +1135,11 @@ __device__ __forceinline__ void adapt_note(TileDigits& a, uint32_t tcount, uint3
 }
 
 // Rank the key-only items of one tile: item i = VK*q + u of thread x is
-// element VK*(q*NT + x) + u, elements [vlo, vhi) are valid; put(i, rank)
-// receives a distinct slot of the key's digit on the counters cnt (0 for an
-// invalid item).  Every thread of the block calls it.
-template <class K, int NT, int KPT, class Put>
+// element VK*(q*NT + x) + u, elements [vlo, vhi) are valid (FULL: the whole
+// tile is, and no item is checked); put(i, rank) receives a distinct slot of
+// the key's digit on the counters cnt (0 for an invalid item).  Every thread
+// of the block calls it.
+template <class K, int NT, int KPT, bool FULL = false, class Put>
 __device__ __forceinline__ void rank_keys_to(const K (&k)[KPT], Put&& put, uint32_t shift, uint32_t vlo,
                                              uint32_t vhi, uint32_t* cnt, const TileDigits& a) {
   constexpr uint32_t VK = 16 / sizeof(K);
@@ -1153,7 +1154,7 @@ __device__ __forceinline__ void rank_keys_to(const K (&k)[KPT], Put&& put, uint3
       const uint32_t dlast = __shfl_sync(FULL, digit_of(k[q * VK + VK - 1], shift), 31);
       bool one = false;
       if (dfirst == dlast) {
-        bool mine = e0 >= vlo && e0 + VK <= vhi;
+        bool mine = FULL || (e0 >= vlo && e0 + VK <= vhi);
 #pragma unroll
         for (int u = 0; u < (int)VK; ++u) mine = mine && digit_of(k[q * VK + u], shift) == dfirst;
         one = __all_sync(FULL, mine);
@@ -1178,7 +1179,7 @@ __device__ __forceinline__ void rank_keys_to(const K (&k)[KPT], Put&& put, uint3
 #pragma unroll
     for (int i = 0; i < KPT; ++i) {
       const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
-      const bool valid = e >= vlo && e < vhi;
+      const bool valid = FULL || (e >= vlo && e < vhi);
       const uint32_t d = digit_of(k[i], shift);
       const bool isdom = valid && d == dom;
       const uint32_t m = __ballot_sync(FULL, isdom);
@@ -1190,6 +1191,9 @@ __device__ __forceinline__ void rank_keys_to(const K (&k)[KPT], Put&& put, uint3
       }
       put(i, isdom ? base + (uint32_t)__popc(m & lt) : (valid ? atomicAdd(&cnt[d], 1u) : 0u));
     }
+  } else if constexpr (FULL) {
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) put(i, atomicAdd(&cnt[digit_of(k[i], shift)], 1u));
   } else {
 #pragma unroll
     for (int i = 0; i < KPT; ++i) {
@@ -1200,10 +1204,10 @@ __device__ __forceinline__ void rank_keys_to(const K (&k)[KPT], Put&& put, uint3
 }
 
 // As rank_keys_to, with the ranks in r[].
-template <class K, int NT, int KPT>
+template <class K, int NT, int KPT, bool FULL = false>
 __device__ __forceinline__ void rank_keys(const K (&k)[KPT], uint32_t (&r)[KPT], uint32_t shift, uint32_t vlo,
                                           uint32_t vhi, uint32_t* cnt, const TileDigits& a) {
-  rank_keys_to<K, NT, KPT>(k, [&](int i, uint32_t v) { r[i] = v; }, shift, vlo, vhi, cnt, a);
+  rank_keys_to<K, NT, KPT, FULL>(k, [&](int i, uint32_t v) { r[i] = v; }, shift, vlo, vhi, cnt, a);
 }
 
 // Decoupled look-back for digit d of tile t (one thread per digit): sums the

@@ -108,7 +108,14 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<NoVal, KPT, false>()))
         k[i] = (e >= vlo && e < vhi) ? src[tb + e] : K(0);
       }
     }
-    rank_keys<K, NT, KPT>(k, r, shift, vlo, vhi, s_cnt, s_ad);
+    // a tile the segment covers whole is ranked and staged without the
+    // per-item bounds (the common case: only a segment's first and last
+    // tiles are partial)
+    const bool full = vlo == 0u && vhi == TILE;
+    if (full)
+      rank_keys<K, NT, KPT, true>(k, r, shift, vlo, vhi, s_cnt, s_ad);
+    else
+      rank_keys<K, NT, KPT, false>(k, r, shift, vlo, vhi, s_cnt, s_ad);
     __syncthreads();
 
     const uint32_t tcount = tid < (uint32_t)M ? s_cnt[tid] : 0u;
@@ -131,18 +138,32 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<NoVal, KPT, false>()))
     }
     __syncthreads();
 
-    // Stage the tile in digit order, each run at its padded start.
+    // Stage the tile in digit order, each run at its padded start (a slot
+    // past the staging area is skipped and reported once).
+    bool bad = false;
+    if (full) {
 #pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-      const uint32_t e = VK * ((uint32_t)(i / VK) * NT + tid) + (uint32_t)(i % VK);
-      if (e >= vlo && e < vhi) {
+      for (int i = 0; i < KPT; ++i) {
         const uint32_t pos = s_pst[digit_of(k[i], shift)] + r[i];
         if (pos < STAGE)
           s_keys[pos] = k[i];
         else
-          record_error(c.ctl, DERR_BOUNDS, ERR_SITE_SCATTER_STAGE);
+          bad = true;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < KPT; ++i) {
+        const uint32_t e = VK * ((uint32_t)(i / VK) * NT + tid) + (uint32_t)(i % VK);
+        if (e >= vlo && e < vhi) {
+          const uint32_t pos = s_pst[digit_of(k[i], shift)] + r[i];
+          if (pos < STAGE)
+            s_keys[pos] = k[i];
+          else
+            bad = true;
+        }
       }
     }
+    if (bad) record_error(c.ctl, DERR_BOUNDS, ERR_SITE_SCATTER_STAGE);
     fence_async_shared();
     __syncthreads();
 
