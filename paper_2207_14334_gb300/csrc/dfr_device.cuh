@@ -469,18 +469,18 @@ __device__ __forceinline__ uint32_t match_digit(uint32_t d) {
 // valid, items i >= kpt are absent): rank[i] = the warp's running count of
 // the digit (kept in `wh`, this warp's private M counters) plus the number of
 // earlier lanes of the same item holding the same digit.  Full-warp
-// operations only.
-template <class K, int KPT>
+// operations only.  FULL: every item is valid (no bounds are checked).
+template <class K, int KPT, bool FULLW = false>
 __device__ __forceinline__ void warp_rank_stable(const K (&k)[KPT], uint32_t shift, uint32_t vlo, uint32_t vhi,
                                                  uint32_t kpt, uint32_t* wh, uint32_t (&rank)[KPT]) {
   const uint32_t lane = lane_id();
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < KPT; ++i) {
-    if ((uint32_t)i < kpt) {
+    if (FULLW || (uint32_t)i < kpt) {
       const uint32_t e = (uint32_t)(i * 32) + lane;
-      const bool valid = e >= vlo && e < vhi;
-      const uint32_t vmask = __ballot_sync(FULL, valid);
+      const bool valid = FULLW || (e >= vlo && e < vhi);
+      const uint32_t vmask = FULLW ? FULL : __ballot_sync(FULL, valid);
       const uint32_t d = digit_of(k[i], shift);
       const uint32_t peers = match_digit(d) & vmask;
       const uint32_t before = valid ? wh[d] : 0u;
@@ -1001,13 +1001,22 @@ __device__ __forceinline__ void level_count_body(const Ctx& c, int L, uint32_t* 
     orv = 0;
     nandv = 0;
   };
-  // a warp claims 1/sub of a tile at a time (as in the root count)
+  // A warp claims 1/sub of a tile at a time (as in the root count).  Claims
+  // map to units column by column -- claim q is unit (q mod W) * rows + q / W
+  // for W warps -- so that a warp's successive claims, about W apart, take
+  // adjacent units, mostly of one segment: its counters then go to the
+  // segment's histogram once per run of units, not once per unit.
   const uint32_t part_keys = (uint32_t)TILE / sub;
+  const uint32_t units = ntiles * sub;
+  const uint32_t nwarps = gridDim.x * (uint32_t)(NT / 32);
+  const uint32_t rows = (units + nwarps - 1u) / nwarps;
   for (;;) {
-    uint32_t u = 0;
-    if (lane == 0) u = atomicAdd(&lc->hist_claim, 1u);
-    u = __shfl_sync(FULL, u, 0);
-    if (u >= ntiles * sub) break;
+    uint32_t q = 0;
+    if (lane == 0) q = atomicAdd(&lc->hist_claim, 1u);
+    q = __shfl_sync(FULL, q, 0);
+    if (q >= nwarps * rows) break;
+    const uint32_t u = (q % nwarps) * rows + q / nwarps;
+    if (u >= units) continue;
     const uint32_t t = u / sub, part = u - t * sub;
     if constexpr (KV) {
       if (part == 0u) {
@@ -1322,49 +1331,59 @@ __device__ __forceinline__ void scatter_body(const Ctx& c, int L) {
     K k[KPT];
     uint32_t r[KPT];
     VT v[KV ? KPT : 1];
-    if constexpr (KV) {
-      // warp-striped: item i of lane l is element wb + i*32 + l
-      const uint32_t wb = warp * 32u * KPT;
-#pragma unroll
-      for (int i = 0; i < KPT; ++i) {
-        const uint32_t e = wb + (uint32_t)(i * 32) + lane;
-        k[i] = K(0);
-        if (e >= vlo && e < vhi) {
-          k[i] = ld_stream(src + tb + e);
-          v[i] = ld_stream(vsrc + tb + e);
-        }
-      }
-      uint32_t* wh = s_cnt + warp * M;
-      const uint32_t wlo = vlo > wb ? vlo - wb : 0u;
-      const uint32_t whi = vhi > wb ? min(vhi - wb, 32u * KPT) : 0u;
-      warp_rank_stable<K, KPT>(k, shift, wlo, whi, KPT, wh, r);
-    } else {
-      // item i = VK * q + u of thread x is element VK * (q * NT + x) + u
-      const bool vec = ((((uintptr_t)src) & 15u) == 0u) && tb + TILE <= ad.n;
-      if (vec) {
-        const uint4* pv = reinterpret_cast<const uint4*>(src + tb);
-#pragma unroll
-        for (int q = 0; q < KPT / (int)VK; ++q) {
-          const uint4 x = __ldcs(pv + q * NT + threadIdx.x);
-          if constexpr (sizeof(K) == 4) {
-            k[q * 4 + 0] = (K)x.x;
-            k[q * 4 + 1] = (K)x.y;
-            k[q * 4 + 2] = (K)x.z;
-            k[q * 4 + 3] = (K)x.w;
-          } else {
-            k[q * 2 + 0] = (K)(((unsigned long long)x.y << 32) | x.x);
-            k[q * 2 + 1] = (K)(((unsigned long long)x.w << 32) | x.z);
-          }
-        }
-      } else {
+    // a tile the segment covers whole is loaded, ranked and staged without
+    // per-item bounds (only a segment's first and last tiles are partial)
+    const bool full = vlo == 0u && vhi == TILE;
+    auto load_rank = [&](auto full_tag) {
+      constexpr bool FL = decltype(full_tag)::value;
+      if constexpr (KV) {
+        // warp-striped: item i of lane l is element wb + i*32 + l
+        const uint32_t wb = warp * 32u * KPT;
 #pragma unroll
         for (int i = 0; i < KPT; ++i) {
-          const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
-          k[i] = (e >= vlo && e < vhi) ? src[tb + e] : K(0);
+          const uint32_t e = wb + (uint32_t)(i * 32) + lane;
+          k[i] = K(0);
+          if (FL || (e >= vlo && e < vhi)) {
+            k[i] = ld_stream(src + tb + e);
+            v[i] = ld_stream(vsrc + tb + e);
+          }
         }
+        uint32_t* wh = s_cnt + warp * M;
+        const uint32_t wlo = vlo > wb ? vlo - wb : 0u;
+        const uint32_t whi = vhi > wb ? min(vhi - wb, 32u * KPT) : 0u;
+        warp_rank_stable<K, KPT, FL>(k, shift, wlo, whi, KPT, wh, r);
+      } else {
+        // item i = VK * q + u of thread x is element VK * (q * NT + x) + u
+        const bool vec = ((((uintptr_t)src) & 15u) == 0u) && tb + TILE <= ad.n;
+        if (vec) {
+          const uint4* pv = reinterpret_cast<const uint4*>(src + tb);
+#pragma unroll
+          for (int q = 0; q < KPT / (int)VK; ++q) {
+            const uint4 x = __ldcs(pv + q * NT + threadIdx.x);
+            if constexpr (sizeof(K) == 4) {
+              k[q * 4 + 0] = (K)x.x;
+              k[q * 4 + 1] = (K)x.y;
+              k[q * 4 + 2] = (K)x.z;
+              k[q * 4 + 3] = (K)x.w;
+            } else {
+              k[q * 2 + 0] = (K)(((unsigned long long)x.y << 32) | x.x);
+              k[q * 2 + 1] = (K)(((unsigned long long)x.w << 32) | x.z);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < KPT; ++i) {
+            const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
+            k[i] = (e >= vlo && e < vhi) ? src[tb + e] : K(0);
+          }
+        }
+        rank_keys<K, NT, KPT, FL>(k, r, shift, vlo, vhi, s_cnt, s_ad);
       }
-      rank_keys<K, NT, KPT>(k, r, shift, vlo, vhi, s_cnt, s_ad);
-    }
+    };
+    if (full)
+      load_rank(std::true_type{});
+    else
+      load_rank(std::false_type{});
     __syncthreads();
 
     // Per digit: tile count (KV: per-warp counts become exclusive offsets).
@@ -1400,30 +1419,40 @@ __device__ __forceinline__ void scatter_body(const Ctx& c, int L) {
     }
     __syncthreads();
 
-    // Stage the tile in shared memory in digit order.
+    // Stage the tile in shared memory in digit order (a slot past the tile
+    // is skipped and reported once).
+    bool bad = false;
+    auto stage = [&](auto full_tag) {
+      constexpr bool FL = decltype(full_tag)::value;
 #pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-      bool valid;
-      uint32_t pos;
-      const uint32_t d = digit_of(k[i], shift);
-      if constexpr (KV) {
-        const uint32_t e = warp * 32u * KPT + (uint32_t)(i * 32) + lane;
-        valid = e >= vlo && e < vhi;
-        pos = s_tstart[d] + s_cnt[warp * M + d] + r[i];
-      } else {
-        const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
-        valid = e >= vlo && e < vhi;
-        pos = s_tstart[d] + r[i];
-      }
-      if (valid) {
-        if (pos < nvalid) {
-          s_keys[pos] = k[i];
-          if constexpr (KV) s_vals[pos] = v[i];
+      for (int i = 0; i < KPT; ++i) {
+        bool valid;
+        uint32_t pos;
+        const uint32_t d = digit_of(k[i], shift);
+        if constexpr (KV) {
+          const uint32_t e = warp * 32u * KPT + (uint32_t)(i * 32) + lane;
+          valid = FL || (e >= vlo && e < vhi);
+          pos = s_tstart[d] + s_cnt[warp * M + d] + r[i];
         } else {
-          record_error(c.ctl, DERR_BOUNDS, ERR_SITE_SCATTER_STAGE);
+          const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
+          valid = FL || (e >= vlo && e < vhi);
+          pos = s_tstart[d] + r[i];
+        }
+        if (valid) {
+          if (pos < nvalid) {
+            s_keys[pos] = k[i];
+            if constexpr (KV) s_vals[pos] = v[i];
+          } else {
+            bad = true;
+          }
         }
       }
-    }
+    };
+    if (full)
+      stage(std::true_type{});
+    else
+      stage(std::false_type{});
+    if (bad) record_error(c.ctl, DERR_BOUNDS, ERR_SITE_SCATTER_STAGE);
     __syncthreads();
 
     // Coalesced write-out of the staged runs.

@@ -152,71 +152,81 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, EST, NT>())) k
     K k[KPT];
     uint32_t r[KPT];
     VT v[KV ? KPT : 1];
-    if constexpr (KV) {
-      // warp-striped: item i of lane l is element wb + i*32 + l
-      const uint32_t wb = warp * 32u * KPT;
-#pragma unroll
-      for (int i = 0; i < KPT; ++i) {
-        const uint32_t e = wb + (uint32_t)(i * 32) + lane;
-        k[i] = K(0);
-        if (e >= vlo && e < vhi) {
-          k[i] = ld_stream(src + tb + e);
-          v[i] = ld_stream(vsrc + tb + e);
-        }
-      }
-      uint32_t* wh = s_cnt + warp * M;
-      const uint32_t wlo = vlo > wb ? vlo - wb : 0u;
-      const uint32_t whi = vhi > wb ? min(vhi - wb, 32u * KPT) : 0u;
-      warp_rank_stable<K, KPT>(k, shift, wlo, whi, KPT, wh, r);
-      if (est) {
+    // a tile the piece covers whole is loaded, ranked and staged without
+    // per-item bounds
+    const bool full = vlo == 0u && vhi == TILE;
+    auto load_rank = [&](auto full_tag) {
+      constexpr bool FL = decltype(full_tag)::value;
+      if constexpr (KV) {
+        // warp-striped: item i of lane l is element wb + i*32 + l
+        const uint32_t wb = warp * 32u * KPT;
 #pragma unroll
         for (int i = 0; i < KPT; ++i) {
           const uint32_t e = wb + (uint32_t)(i * 32) + lane;
-          if (e >= vlo && e < vhi) {
-            atomicAdd(&s_h0[digit_of(k[i], W - RB)], 1u);
-            orv |= k[i];
-            nandv |= ~k[i];
+          k[i] = K(0);
+          if (FL || (e >= vlo && e < vhi)) {
+            k[i] = ld_stream(src + tb + e);
+            v[i] = ld_stream(vsrc + tb + e);
           }
         }
-      }
-    } else {
-      // item i = VK * q + u of thread x is element VK * (q * NT + x) + u
-      const bool vec = ((((uintptr_t)src) & 15u) == 0u) && vlo == 0u && vhi == TILE;
-      if (vec) {
-        const uint4* pv = reinterpret_cast<const uint4*>(src + tb);
+        uint32_t* wh = s_cnt + warp * M;
+        const uint32_t wlo = vlo > wb ? vlo - wb : 0u;
+        const uint32_t whi = vhi > wb ? min(vhi - wb, 32u * KPT) : 0u;
+        warp_rank_stable<K, KPT, FL>(k, shift, wlo, whi, KPT, wh, r);
+        if (est) {
 #pragma unroll
-        for (int q = 0; q < KPT / (int)VK; ++q) {
-          const uint4 x = __ldcs(pv + q * NT + threadIdx.x);
-          if constexpr (sizeof(K) == 4) {
-            k[q * 4 + 0] = (K)x.x;
-            k[q * 4 + 1] = (K)x.y;
-            k[q * 4 + 2] = (K)x.z;
-            k[q * 4 + 3] = (K)x.w;
-          } else {
-            k[q * 2 + 0] = (K)(((unsigned long long)x.y << 32) | x.x);
-            k[q * 2 + 1] = (K)(((unsigned long long)x.w << 32) | x.z);
+          for (int i = 0; i < KPT; ++i) {
+            const uint32_t e = wb + (uint32_t)(i * 32) + lane;
+            if (FL || (e >= vlo && e < vhi)) {
+              atomicAdd(&s_h0[digit_of(k[i], W - RB)], 1u);
+              orv |= k[i];
+              nandv |= ~k[i];
+            }
           }
         }
       } else {
+        // item i = VK * q + u of thread x is element VK * (q * NT + x) + u
+        const bool vec = ((((uintptr_t)src) & 15u) == 0u) && vlo == 0u && vhi == TILE;
+        if (vec) {
+          const uint4* pv = reinterpret_cast<const uint4*>(src + tb);
 #pragma unroll
-        for (int i = 0; i < KPT; ++i) {
-          const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
-          k[i] = (e >= vlo && e < vhi) ? src[tb + e] : K(0);
+          for (int q = 0; q < KPT / (int)VK; ++q) {
+            const uint4 x = __ldcs(pv + q * NT + threadIdx.x);
+            if constexpr (sizeof(K) == 4) {
+              k[q * 4 + 0] = (K)x.x;
+              k[q * 4 + 1] = (K)x.y;
+              k[q * 4 + 2] = (K)x.z;
+              k[q * 4 + 3] = (K)x.w;
+            } else {
+              k[q * 2 + 0] = (K)(((unsigned long long)x.y << 32) | x.x);
+              k[q * 2 + 1] = (K)(((unsigned long long)x.w << 32) | x.z);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < KPT; ++i) {
+            const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
+            k[i] = (e >= vlo && e < vhi) ? src[tb + e] : K(0);
+          }
         }
-      }
-      rank_keys<K, NT, KPT>(k, r, shift, vlo, vhi, s_cnt, s_ad);
-      if (est) {
+        rank_keys<K, NT, KPT, FL>(k, r, shift, vlo, vhi, s_cnt, s_ad);
+        if (est) {
 #pragma unroll
-        for (int i = 0; i < KPT; ++i) {
-          const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
-          if (e >= vlo && e < vhi) {
-            atomicAdd(&s_h0[digit_of(k[i], W - RB)], 1u);
-            orv |= k[i];
-            nandv |= ~k[i];
+          for (int i = 0; i < KPT; ++i) {
+            const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
+            if (FL || (e >= vlo && e < vhi)) {
+              atomicAdd(&s_h0[digit_of(k[i], W - RB)], 1u);
+              orv |= k[i];
+              nandv |= ~k[i];
+            }
           }
         }
       }
-    }
+    };
+    if (full)
+      load_rank(std::true_type{});
+    else
+      load_rank(std::false_type{});
     __syncthreads();
 
     // Per digit: tile count (key-value: per-warp counts become exclusive
@@ -268,30 +278,40 @@ __global__ void __launch_bounds__(NT, (scatter_min_blocks<V, KPT, EST, NT>())) k
     }
     __syncthreads();
 
-    // Stage the tile in shared memory in digit order.
+    // Stage the tile in shared memory in digit order (a slot past the tile
+    // is skipped and reported once).
+    bool bad = false;
+    auto stage = [&](auto full_tag) {
+      constexpr bool FL = decltype(full_tag)::value;
 #pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-      bool valid;
-      uint32_t pos;
-      const uint32_t d = digit_of(k[i], shift);
-      if constexpr (KV) {
-        const uint32_t e = warp * 32u * KPT + (uint32_t)(i * 32) + lane;
-        valid = e >= vlo && e < vhi;
-        pos = s_tstart[d] + s_cnt[warp * M + d] + r[i];
-      } else {
-        const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
-        valid = e >= vlo && e < vhi;
-        pos = s_tstart[d] + r[i];
-      }
-      if (valid) {
-        if (pos < nvalid) {
-          s_keys[pos] = k[i];
-          if constexpr (KV) s_vals[pos] = v[i];
+      for (int i = 0; i < KPT; ++i) {
+        bool valid;
+        uint32_t pos;
+        const uint32_t d = digit_of(k[i], shift);
+        if constexpr (KV) {
+          const uint32_t e = warp * 32u * KPT + (uint32_t)(i * 32) + lane;
+          valid = FL || (e >= vlo && e < vhi);
+          pos = s_tstart[d] + s_cnt[warp * M + d] + r[i];
         } else {
-          record_error(c.ctl, DERR_BOUNDS, ERR_SITE_LSD_STAGE);
+          const uint32_t e = VK * ((uint32_t)(i / VK) * NT + threadIdx.x) + (uint32_t)(i % VK);
+          valid = FL || (e >= vlo && e < vhi);
+          pos = s_tstart[d] + r[i];
+        }
+        if (valid) {
+          if (pos < nvalid) {
+            s_keys[pos] = k[i];
+            if constexpr (KV) s_vals[pos] = v[i];
+          } else {
+            bad = true;
+          }
         }
       }
-    }
+    };
+    if (full)
+      stage(std::true_type{});
+    else
+      stage(std::false_type{});
+    if (bad) record_error(c.ctl, DERR_BOUNDS, ERR_SITE_LSD_STAGE);
     __syncthreads();
 
     // Coalesced write-out of the staged runs.
