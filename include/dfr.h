@@ -395,8 +395,9 @@ typedef struct {
 } dfr_tune_t;
 
 /*
- * Launch forms of a plain call or a dfr_sort_batch call (the served form
- * always uses the level sequence).  Both give the same result.
+ * Launch forms of a plain call or a dfr_sort_batch call (a server with more
+ * than one stream always uses the level sequence).  Both give the same
+ * result.
  *   DFR_LAUNCH_AUTO        one persistent launch for calls of fewer than
  *                          DFR_PERSIST_AUTO_KEYS keys in all, the level
  *                          sequence otherwise;

@@ -247,10 +247,12 @@ void dfr_server::launch(Batch* b, std::vector<dfr_segment_t>& segs) {
     std::vector<HostArr> arrs(segs.size());
     for (size_t i = 0; i < segs.size(); ++i)
       arrs[i] = HostArr{segs[i].keys, segs[i].kbuf, segs[i].vals, segs[i].vbuf, segs[i].n};
-    // the level sequence: batches on several streams run side by side,
-    // which a cooperative launch's whole-grid residency would serialise
+    // With several streams the batches take the level sequence: they run side
+    // by side, which a cooperative launch's whole-grid residency would
+    // serialise.  A one-stream server runs its batches one after another, as
+    // plain calls do, so it takes their launch form.
     rc = run_typed(segs[0].key_type, arrs.data(), (uint32_t)arrs.size(), arrs.size() > 1, ws, b->bytes, st,
-                   DFR_FMT_UNSIGNED, false);
+                   DFR_FMT_UNSIGNED, streams.size() == 1);
   }
   bool any = false;
   for (const auto& g : segs) any = any || g.n > 1;
