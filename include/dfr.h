@@ -412,7 +412,7 @@ typedef struct {
  * The LSD schedules of the top digits always run as the level sequence.
  */
 enum dfr_launch { DFR_LAUNCH_AUTO = 0, DFR_LAUNCH_LEVELS = 1, DFR_LAUNCH_PERSISTENT = 2 };
-#define DFR_PERSIST_AUTO_KEYS ((uint64_t)1 << 22)
+#define DFR_PERSIST_AUTO_KEYS ((uint64_t)1 << 25)
 
 /*
  * Schedules of the top digits (paper, Section "Diverting Fast Radix").

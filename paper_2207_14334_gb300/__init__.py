@@ -63,7 +63,7 @@ DFR_SCHED_DFR = 2
 DFR_LAUNCH_AUTO = 0
 DFR_LAUNCH_LEVELS = 1
 DFR_LAUNCH_PERSISTENT = 2
-DFR_PERSIST_AUTO_KEYS = 1 << 22
+DFR_PERSIST_AUTO_KEYS = 1 << 25
 
 KEY_BYTES = {DFR_U32: 4, DFR_U64: 8, DFR_U64_KV: 8, DFR_U32_KV: 4, DFR_U64_KV64: 8, DFR_U32_KV64: 4}
 VAL_BYTES = {DFR_U32: 0, DFR_U64: 0, DFR_U64_KV: 4, DFR_U32_KV: 4, DFR_U64_KV64: 8, DFR_U32_KV64: 8}
