@@ -597,13 +597,13 @@ __global__ void k_init(Ctx c, ArrDesc a0, int write_a0, uint32_t root_words, uin
 
 // Warp-level streaming count over keys src[lo, hi): 128-bit loads (batches
 // of 8 vectors per lane in flight), one shared atomic per key on the warp's
-// private counters `wh` at digit (key >> shift) & (M-1) when do_hist (lanes
+// private counters `wh` at digit (key >> shift) & (M-1) when HIST (lanes
 // that hit one counter are serialised by the hardware, which measured faster
 // than aggregating them in software on every input, skewed or sorted ones
 // included), and OR / NOT-AND of the keys into orv / nandv.
-template <class K, bool TWO = false>
+template <class K, bool TWO = false, bool HIST = true>
 __device__ __forceinline__ void warp_count_range(const K* src, uint32_t lo, uint32_t hi, uint32_t shift,
-                                                 bool do_hist, uint32_t* wh, K& orv, K& nandv,
+                                                 uint32_t* wh, K& orv, K& nandv,
                                                  uint32_t* wh2 = nullptr, uint32_t shift2 = 0) {
   constexpr uint32_t VK = 16 / sizeof(K);
   constexpr int BATCH = 8;
@@ -617,7 +617,7 @@ __device__ __forceinline__ void warp_count_range(const K* src, uint32_t lo, uint
       orv |= k;
       nandv |= ~k;
     }
-    if (do_hist && valid) atomicAdd(&wh[digit_of(k, shift)], 1u);
+    if (HIST && valid) atomicAdd(&wh[digit_of(k, shift)], 1u);
     if constexpr (TWO) {
       if (valid) atomicAdd(&wh2[digit_of(k, shift2)], 1u);
     }
@@ -628,7 +628,27 @@ __device__ __forceinline__ void warp_count_range(const K* src, uint32_t lo, uint
   }
   const uint32_t nv = (n - head) / VK;
   const uint4* pv = reinterpret_cast<const uint4*>(p + head);
-  for (uint32_t b = 0; b < nv; b += 32u * BATCH) {
+  // whole batches first, with no per-vector bound (the common case), then
+  // the last partial batch
+  const uint32_t nfull = nv / (32u * BATCH) * (32u * BATCH);
+  for (uint32_t b = 0; b < nfull; b += 32u * BATCH) {
+    uint4 x[BATCH];
+#pragma unroll
+    for (int q = 0; q < BATCH; ++q) x[q] = __ldcs(pv + b + (uint32_t)q * 32u + lane);
+#pragma unroll
+    for (int q = 0; q < BATCH; ++q) {
+      if constexpr (sizeof(K) == 4) {
+        one((K)x[q].x, true);
+        one((K)x[q].y, true);
+        one((K)x[q].z, true);
+        one((K)x[q].w, true);
+      } else {
+        one((K)(((unsigned long long)x[q].y << 32) | x[q].x), true);
+        one((K)(((unsigned long long)x[q].w << 32) | x[q].z), true);
+      }
+    }
+  }
+  for (uint32_t b = nfull; b < nv; b += 32u * BATCH) {
     uint4 x[BATCH];
 #pragma unroll
     for (int q = 0; q < BATCH; ++q) {
@@ -785,7 +805,7 @@ __device__ __forceinline__ void root_count_body(const Ctx& c, uint32_t root_tile
     const uint32_t b = j * (uint32_t)TILE + part * part_keys;
     const uint32_t e = min(ad.n, b + part_keys);
     if (b < e)
-      warp_count_range<K, TWO>(reinterpret_cast<const K*>(ad.keys), b, e, TOP, true, wh, orv, nandv, wh2, TOP - RB);
+      warp_count_range<K, TWO, true>(reinterpret_cast<const K*>(ad.keys), b, e, TOP, wh, orv, nandv, wh2, TOP - RB);
   }
   if constexpr (TWO) {
     flush();
@@ -1050,7 +1070,10 @@ __device__ __forceinline__ void level_count_body(const Ctx& c, int L, uint32_t* 
     const uint32_t b = max(pb, seg.off);
     const uint32_t e = min(seg.off + seg.len, pb + part_keys);
     if (b >= e) continue;
-    warp_count_range<K>(src, b, e, seg.shift, (flags & SEG_NEEDS_HIST) != 0u, wh, orv, nandv);
+    if (flags & SEG_NEEDS_HIST)
+      warp_count_range<K, false, true>(src, b, e, seg.shift, wh, orv, nandv);
+    else
+      warp_count_range<K, false, false>(src, b, e, seg.shift, wh, orv, nandv);
     keys_read += e - b;
   }
   cta_merge_counts<K, NT / 32>(
