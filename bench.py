@@ -1010,11 +1010,37 @@ def run_plain(args, wl, dfr, dev, world, rank, emit=True):
             if st != dfr.DFR_OK:
                 raise RuntimeError("device status %s in the end-to-end run" % dfr.dfr_status_string(st))
         ms, e2e_rate = job_rate(sum(e2e_ms) / len(e2e_ms), keys_per_step, world, dev)
+        # The host link of this machine, for context: one array's plain
+        # copy each way from / to the same pinned buffers, and both at once.
+        first = next(iter(inputs))
+        nbytes = host_in[first].numel() * host_in[first].element_size()
+
+        def copy_ms(pairs):
+            torch.cuda.synchronize()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(streams[0])
+            for s in streams[1:]:
+                s.wait_event(c0)
+            for j, (dst_t, src_t) in enumerate(pairs):
+                with torch.cuda.stream(streams[j % ns]):
+                    dst_t.copy_(src_t, non_blocking=True)
+            for s in streams[1:]:
+                ev = torch.cuda.Event()
+                ev.record(s)
+                streams[0].wait_event(ev)
+            c1.record(streams[0])
+            c1.synchronize()
+            return c0.elapsed_time(c1)
+
+        h2d = nbytes / (copy_ms([(works[0], host_in[first])]) * 1e-3) / 1e9
+        d2h = nbytes / (copy_ms([(host_out[0], works[0])]) * 1e-3) / 1e9
+        both = 2 * nbytes / (copy_ms([(works[0], host_in[first]), (host_out[-1], works[-1])]) * 1e-3) / 1e9
         e2e = {"value": e2e_rate, "unit": "Gkeys/s",
                "h2d_bytes_per_step": keys_per_step * rec, "d2h_bytes_per_step": keys_per_step * rec,
                "ms_per_step": ms, "streams": ns,
                "overlap": "arrays round-robin over %d streams: uploads, sorts and downloads of consecutive arrays "
-                          "overlap" % ns}
+                          "overlap" % ns,
+               "host_link_gbs": {"h2d": h2d, "d2h": d2h, "both_directions": both}}
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample > 0:
