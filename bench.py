@@ -709,7 +709,7 @@ def run_served(args, wl, dfr, dev, world, rank):
     closed_plain = one(False, None, min(R, 20_000))
 
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
         cpu = cpu_served_time(wl, args.cpu_sample, R)
     if rank == 0:
         full = loads["100%"]
