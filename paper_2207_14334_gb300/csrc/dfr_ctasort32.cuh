@@ -54,15 +54,39 @@ struct Cta32 {
   static constexpr uint32_t SPANMAX = B1MAX + 4;          // widest span sorted here
   static_assert(SPANMAX == CTA32_SPAN, "the classifiers route by the same span");
   static constexpr size_t slot_bytes = ((size_t)CAP + 8) * 4;
-  static constexpr uint32_t NIBW = 2u << B1MAX;           // nibble-counter words: two per 12-bit group
-  static constexpr size_t cnt1_bytes = ((size_t)NIBW + 4) * 4;  // first-pass counters or nibble counters
-  static constexpr size_t start_bytes = (size_t)(1u << B1MAX) * 4;  // group starts of the nibble pass
-  static constexpr size_t smem_bytes = STAGES * slot_bytes + cnt1_bytes + start_bytes;
+  // Nibble-pass layout: block b holds the counter words of the 12-bit groups
+  // [8b, 8b + 8) (two per group) and then their 16-bit starts, 20 words in
+  // all.  In the scan a thread owns one block; at the 80-byte block stride
+  // the 16-byte accesses of eight consecutive threads fall in distinct banks.
+  static constexpr uint32_t GPB = 8;                                  // groups per block
+  static constexpr uint32_t BLKW = 2 * GPB + GPB / 2;                 // words per block
+  static constexpr uint32_t NIBW = BLKW * ((1u << B1MAX) / GPB);      // 10,240
+  static constexpr size_t cnt1_bytes = ((size_t)NIBW + 4) * 4;  // first-pass counters or nibble blocks
+  static constexpr size_t smem_bytes = STAGES * slot_bytes + cnt1_bytes;
 };
+
+// Word of the nibble-counter block layout where 12-bit group g's counters start.
+__device__ __forceinline__ uint32_t nib_word(uint32_t g) { return (g >> 3) * 20u + (g & 7u) * 2u; }
 
 template <int NC, int NV, int STAGES>
 constexpr size_t ctasort32_smem_bytes() {
   return Cta32<NC, NV, STAGES>::smem_bytes;
+}
+
+// Sum of wsum[w] over the warps w < warp (wsum: one total per warp of the
+// NW <= 32 warps): one shared load per lane and a warp scan, the same value
+// in every lane of the warp.
+template <int NW>
+__device__ __forceinline__ uint32_t warps_before(const uint32_t* wsum, uint32_t warp, uint32_t lane) {
+  static_assert(NW <= 32, "one warp total per lane");
+  const uint32_t x = lane < (uint32_t)NW ? wsum[lane] : 0u;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < NW; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, inc, o);
+    if (lane >= (uint32_t)o) inc += y;
+  }
+  return __shfl_sync(FULL, inc - x, warp);
 }
 
 // Exclusive scan of the n counters c[0, n) in place (n a power of two; each
@@ -96,9 +120,7 @@ __device__ __forceinline__ void scan_counters(uint32_t* c, uint32_t n, uint32_t*
   }
   if (lane == 31) wsum[warp] = inc;
   named_sync(1, NC);
-  uint32_t base = inc - tot;
-#pragma unroll
-  for (int w = 0; w < NW; ++w) base += (uint32_t)w < warp ? wsum[w] : 0u;
+  uint32_t base = inc - tot + warps_before<NW>(wsum, warp, lane);
   if (owns) {
     if (E >= 4u) {
       for (uint32_t k = 0; k < E; k += 4u) {
@@ -122,10 +144,11 @@ __device__ __forceinline__ void scan_counters(uint32_t* c, uint32_t n, uint32_t*
   }
 }
 
-// Sum of the eight 4-bit fields of x (at most 8 x 15).
-__device__ __forceinline__ uint32_t nib_sum(uint32_t x) {
-  const uint32_t b = (x & 0x0F0F0F0Fu) + ((x >> 4) & 0x0F0F0F0Fu);  // four byte sums <= 30
-  return (b * 0x01010101u) >> 24;
+// Sum of the sixteen 4-bit fields of x and y (at most 16 x 15).
+__device__ __forceinline__ uint32_t nib_sum2(uint32_t x, uint32_t y) {
+  const uint32_t b = (x & 0x0F0F0F0Fu) + ((x >> 4) & 0x0F0F0F0Fu) + (y & 0x0F0F0F0Fu) +
+                     ((y >> 4) & 0x0F0F0F0Fu);  // four byte sums <= 60
+  return (b * 0x01010101u) >> 24;              // no byte of the partial sums passes 240
 }
 
 // What the producer hands the consumers with each slot.
@@ -144,7 +167,8 @@ __global__ void __launch_bounds__(NC + 32, MINB) k_ctasort32(Ctx c) {
   constexpr int NW = P::NW;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint32_t* s_cnt1 = reinterpret_cast<uint32_t*>(smem_raw + STAGES * P::slot_bytes);
-  uint32_t* s_start = reinterpret_cast<uint32_t*>(smem_raw + STAGES * P::slot_bytes + P::cnt1_bytes);  // [4096]
+  static_assert(P::BLKW == 20u && P::GPB == 8u, "nib_word's block layout");
+  static_assert(P::slot_bytes % 16 == 0, "16-byte aligned counter blocks");
   __shared__ __align__(8) uint64_t s_full[STAGES], s_empty[STAGES];
   __shared__ SlotMeta s_meta[STAGES];
   __shared__ uint32_t s_or[2], s_and[2], s_ovf[2];
@@ -304,13 +328,11 @@ __global__ void __launch_bounds__(NC + 32, MINB) k_ctasort32(Ctx c) {
           uint32_t dupw[(NV * 4 + 1 + 7) / 8];  // 4-bit counts of earlier equal keys, eight to a register
 #pragma unroll
           for (int i = 0; i < (NV * 4 + 1 + 7) / 8; ++i) dupw[i] = 0u;
-          bool ovf = false;
           auto nib_add = [&](uint32_t k, int slot) {
             const uint32_t g = (k >> gshift) & 4095u, lo = (k >> lb) & lmask;
             const uint32_t shf = 4u * (lo & 7u);
-            const uint32_t old = atomicAdd(&s_cnt1[2u * g + (lo >> 3)], 1u << shf);
+            const uint32_t old = atomicAdd(&s_cnt1[nib_word(g) + (lo >> 3)], 1u << shf);
             const uint32_t dup = (old >> shf) & 15u;
-            ovf = ovf || dup == 15u;
             dupw[slot / 8] |= dup << (4 * (slot % 8));
           };
 #pragma unroll
@@ -324,20 +346,30 @@ __global__ void __launch_bounds__(NC + 32, MINB) k_ctasort32(Ctx c) {
             }
           }
           if (has_e) nib_add(xe, NV * 4);
-          if (ovf) s_ovf[p] = 1u;
+          {  // a count of 15 earlier equal keys: the counter is full
+            uint32_t full = 0u;
+#pragma unroll
+            for (int i = 0; i < (NV * 4 + 1 + 7) / 8; ++i) {
+              const uint32_t t = dupw[i] & (dupw[i] >> 1);
+              full |= t & (t >> 2);
+            }
+            if (full & 0x11111111u) s_ovf[p] = 1u;
+          }
           named_sync(1, NC);
           if (!s_ovf[p]) {
-            // Group totals and their exclusive scan: thread t owns groups
-            // [8t, 8t + 8) (16 counter words); starts go to s_start.
-            static_assert((4096 / NC) * NC == 4096 && 4096 / NC <= 8, "whole groups per thread");
-            constexpr uint32_t GPT = 4096u / NC;
+            // Group totals and their exclusive scan: thread t owns block t,
+            // groups [8t, 8t + 8); their starts go to the block's last four
+            // words, two 16-bit starts to a word.
+            static_assert(NC * P::GPB == 4096u, "one counter block per thread");
+            constexpr uint32_t GPT = P::GPB;
+            uint4* blk = reinterpret_cast<uint4*>(s_cnt1 + tid * P::BLKW);
             uint32_t gt[GPT];
             uint32_t tot = 0u;
 #pragma unroll
             for (uint32_t q = 0; q < GPT; q += 2u) {
-              const uint4 w = *reinterpret_cast<const uint4*>(s_cnt1 + 2u * (tid * GPT + q));
-              gt[q] = nib_sum(w.x) + nib_sum(w.y);
-              gt[q + 1] = nib_sum(w.z) + nib_sum(w.w);
+              const uint4 w = blk[q / 2u];
+              gt[q] = nib_sum2(w.x, w.y);
+              gt[q + 1] = nib_sum2(w.z, w.w);
               tot += gt[q] + gt[q + 1];
             }
             uint32_t inc = tot;
@@ -348,21 +380,23 @@ __global__ void __launch_bounds__(NC + 32, MINB) k_ctasort32(Ctx c) {
             }
             if (lane == 31) s_wsum[p][0][warp] = inc;
             named_sync(1, NC);
-            uint32_t base = inc - tot;
+            uint32_t base = inc - tot + warps_before<NW>(s_wsum[p][0], warp, lane);
+            uint32_t st[GPT / 2];  // starts < CAP <= 65536
 #pragma unroll
-            for (int w = 0; w < NW; ++w) base += (uint32_t)w < warp ? s_wsum[p][0][w] : 0u;
-#pragma unroll
-            for (uint32_t q = 0; q < GPT; ++q) {
-              s_start[tid * GPT + q] = base;
-              base += gt[q];
+            for (uint32_t q = 0; q < GPT; q += 2u) {
+              st[q / 2u] = base | ((base + gt[q]) << 16);
+              base += gt[q] + gt[q + 1];
             }
+            blk[GPT / 2u] = make_uint4(st[0], st[1], st[2], st[3]);
             named_sync(1, NC);
             auto place = [&](uint32_t k, int slot) {
               const uint32_t g = (k >> gshift) & 4095u, lo = (k >> lb) & lmask;
-              const uint2 w = *reinterpret_cast<const uint2*>(s_cnt1 + 2u * g);
-              const uint32_t m = (1u << (4u * (lo & 7u))) - 1u;
-              const uint32_t below = lo < 8u ? nib_sum(w.x & m) : nib_sum(w.x) + nib_sum(w.y & m);
-              const uint32_t pos = s_start[g] + below + ((dupw[slot / 8] >> (4 * (slot % 8))) & 15u);
+              const uint32_t bw = (g >> 3) * P::BLKW;
+              const uint2 w = *reinterpret_cast<const uint2*>(s_cnt1 + bw + (g & 7u) * 2u);
+              const uint32_t gs = reinterpret_cast<const uint16_t*>(s_cnt1)[2u * (bw + 2u * P::GPB) + (g & 7u)];
+              const unsigned long long m = (1ull << (4u * lo)) - 1ull;  // the counters of lower values
+              const uint32_t below = nib_sum2(w.x & (uint32_t)m, w.y & (uint32_t)(m >> 32));
+              const uint32_t pos = gs + below + ((dupw[slot / 8] >> (4 * (slot % 8))) & 15u);
               if (pos < len)
                 s_keys[osh + pos] = k;
               else
@@ -382,8 +416,12 @@ __global__ void __launch_bounds__(NC + 32, MINB) k_ctasort32(Ctx c) {
             done = true;
           }
           named_sync(1, NC);
-          for (uint32_t i = tid * 4u; i < P::NIBW; i += NC * 4u)  // for the next bucket
-            *reinterpret_cast<uint4*>(s_cnt1 + i) = make_uint4(0u, 0u, 0u, 0u);
+          {  // for the next bucket: counters and starts (the 12-bit pass counts in the same words)
+            static_assert(NC * P::BLKW == P::NIBW, "one block per thread");
+            uint4* blk = reinterpret_cast<uint4*>(s_cnt1 + tid * P::BLKW);
+#pragma unroll
+            for (uint32_t j = 0; j < P::BLKW / 4u; ++j) blk[j] = make_uint4(0u, 0u, 0u, 0u);
+          }
         }
         if (!done && span <= P::B1MAX) {
           // One counting pass on every varying bit: the staged order is final.

@@ -143,3 +143,39 @@ def test_forced_timeout_reports_and_recovers(dfr):
     assert st == dfr.DFR_OK
     ok, ov = oracle.sort_u32_kv(a, v)
     assert np.array_equal(k, ok) and np.array_equal(vv, ov)
+
+
+def test_cta32_counter_boundaries(dfr):
+    """Buckets of ~4000 u32 keys whose keys vary in the low 13..16 bits go to
+    the fast CTA sort, which counts each value in a 4-bit counter: a value
+    seen 15 times fits, the 16th copy sends the bucket to the general CTA
+    sort.  One bucket per top byte, each at one side of that boundary (and
+    spans of 13 and 16 bits), in both launch forms, against the oracle."""
+    from test_gpu_persist import launch_form
+
+    g = np.random.Generator(np.random.PCG64(1234))
+
+    def bucket(top, nbits, reps):
+        hi = (1 << nbits) - 1
+        special = [int(x) for x in 1 + g.choice(hi - 1, size=len(reps), replace=False)]
+        pool = np.setdiff1d(np.arange(1, hi, dtype=np.uint32), np.array(special, dtype=np.uint32))
+        low = [np.array([0, hi], dtype=np.uint32), g.choice(pool, size=4000 - 2 - sum(reps), replace=False)]
+        low += [np.full(r, s, dtype=np.uint32) for s, r in zip(special, reps)]
+        return (np.uint32(top) << np.uint32(24)) | np.concatenate(low).astype(np.uint32)
+
+    parts = [
+        bucket(0x11, 16, [15]),          # 15 copies: the counter is full, not past it
+        bucket(0x22, 16, [16]),          # 16 copies: second queue
+        bucket(0x33, 16, [15, 15, 15]),  # several full counters in one bucket
+        bucket(0x44, 13, [15, 14]),      # 13-bit span (one low bit per group)
+        bucket(0x55, 13, [17]),
+        bucket(0x66, 16, [40, 15, 2]),
+    ]
+    a = np.concatenate(parts)
+    a = a[g.permutation(a.size)]
+    want = oracle.sort_u32(a)
+    for launch in (dfr.DFR_LAUNCH_LEVELS, dfr.DFR_LAUNCH_PERSISTENT):
+        with launch_form(dfr, launch, (dfr.DFR_U32,)):
+            k, _, st = gpu_sort(dfr, a)
+        assert st == dfr.DFR_OK
+        assert np.array_equal(k, want), launch
