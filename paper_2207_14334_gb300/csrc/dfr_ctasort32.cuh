@@ -9,10 +9,10 @@
 // Warp roles.  One producer warp runs ahead of the sort: it claims the next
 // bucket from the queue, reads its descriptor and starts an asynchronous bulk
 // copy (cp.async.bulk, global -> shared, completing on an mbarrier) of the
-// bucket's 16-byte-aligned interior into a free slot of a STAGES-deep ring.
-// The NC consumer threads sort the bucket of the oldest full slot (reading
-// the unaligned head and tail, at most three keys each, from global memory)
-// and hand the slot back.  So the claim, descriptor and key latencies of a
+// bucket's 16-byte-aligned interior into a free slot of a STAGES-deep ring,
+// and reads its unaligned head and tail (at most three keys each) into the
+// slot's descriptor.  The NC consumer threads sort the bucket of the oldest
+// full slot and hand the slot back.  So the claim, descriptor and key latencies of a
 // bucket overlap the sort of the previous one.  Consumer phases synchronise
 // on a named barrier that the producer warp does not join.
 //
@@ -155,8 +155,9 @@ __device__ __forceinline__ uint32_t nib_sum2(uint32_t x, uint32_t y) {
 struct SlotMeta {
   Item item;       // the queue item (item.arr = NO_OWNER: no more buckets)
   const uint32_t* src;
-  uint32_t head;   // keys before the first 16-byte boundary (read from global)
-  uint32_t nvec;   // 16-byte vectors copied into the slot
+  uint32_t head;     // keys before the first 16-byte boundary
+  uint32_t nvec;     // 16-byte vectors copied into the slot
+  uint32_t edge[6];  // the head keys, then the tail keys past the last vector (at most 3 each)
 };
 
 template <int NC, int NV, int STAGES, int MINB>
@@ -216,6 +217,10 @@ __global__ void __launch_bounds__(NC + 32, MINB) k_ctasort32(Ctx c) {
           if (!(m.item.info & ITEM_COPY)) {
             m.head = min(len, (uint32_t)((16u - ((uint32_t)(uintptr_t)m.src & 15u)) & 15u) / 4u);
             m.nvec = (len - m.head) / 4u;
+            // the ragged ends, read here so that the sort does not wait for them
+            const uint32_t tb = m.head + m.nvec * 4u;
+            for (uint32_t e = 0; e < m.head; ++e) m.edge[e] = m.src[e];
+            for (uint32_t e = tb; e < len; ++e) m.edge[m.head + (e - tb)] = m.src[e];
           }
         }
         s_meta[s] = m;
@@ -283,7 +288,7 @@ __global__ void __launch_bounds__(NC + 32, MINB) k_ctasort32(Ctx c) {
       }
       const bool has_e = tid < head + tail;
       if (has_e) {
-        xe = tid < head ? src[tid] : src[head + nvec * 4u + (tid - head)];
+        xe = s_meta[slot].edge[tid];
         orv |= xe;
         andv &= xe;
       }
