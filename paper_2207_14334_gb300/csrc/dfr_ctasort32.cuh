@@ -327,7 +327,8 @@ __global__ void __launch_bounds__(NC + 32, MINB) k_ctasort32(Ctx c) {
           // bits) counter and returns how many equal keys came first; the
           // final position is the group's start + the keys of the group with
           // smaller low bits + that count.  A counter that would pass 15
-          // (more than 15 equal keys) sends the bucket to the LSD passes.
+          // (more than 15 equal keys) sends the bucket to the general CTA
+          // sort (second queue).
           const uint32_t L = span - P::B1MAX;
           const uint32_t gshift = lb + L, lmask = (1u << L) - 1u;
           uint32_t dupw[(NV * 4 + 1 + 7) / 8];  // 4-bit counts of earlier equal keys, eight to a register
