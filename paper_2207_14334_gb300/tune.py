@@ -11,6 +11,13 @@ fastest.  The plans never change a result, only the time.
 For single arrays of at least dfr_lsd_min_keys keys it also tries the LSD
 schedule of the top digits (Algorithm 4) on top of the best MSD plan.
 
+The table serves both launch forms: a call of fewer than
+DFR_PERSIST_AUTO_KEYS keys runs as one persistent launch, a larger one (a
+big batch of the same mean length) as the level sequence.  With --both-forms
+a class whose timing workload is small enough for the persistent form is
+timed in both forms, and the plan kept is the one with the smallest mean of
+its two times, each divided by the best time of its form (pick_plan).
+
 Writes the table as JSON and as the C include compiled into the library
 (csrc/dfr_tune_table.inc); rebuild afterwards.  Needs a GPU:
 
@@ -48,6 +55,16 @@ def candidates(cap_log2: int):
         out.append(dict(target_log2=tl, max_bits=mb, warp_max=wm, scatter_ctas_per_sm=sc, ctasort_ctas_per_sm=cs,
                         schedule=0))
     return out
+
+
+def pick_plan(times):
+    """The plan to keep from {plan key: {form: ms}}: the smallest mean over
+    the forms it was timed in of ms / (the best ms of that form)."""
+    best = {}
+    for t in times.values():
+        for form, ms in t.items():
+            best[form] = min(ms, best.get(form, ms))
+    return min(times, key=lambda k: sum(ms / best[f] for f, ms in times[k].items()) / len(times[k]))
 
 
 class Case:
@@ -99,7 +116,7 @@ class Case:
         return ts[len(ts) // 2]
 
 
-def tune(key_types, classes, reps: int, budget_keys: int, schedules=(0, 1), log=print):
+def tune(key_types, classes, reps: int, budget_keys: int, schedules=(0, 1), both_forms=False, log=print):
     import torch
 
     import paper_2207_14334_gb300 as dfr
@@ -113,13 +130,17 @@ def tune(key_types, classes, reps: int, budget_keys: int, schedules=(0, 1), log=
             n = class_length(c)
             count = max(1, min(4096, budget_keys // n))
             case = Case(dfr, torch, kt, n, count, seed=0x5EED0000 + 1000 * c + kt)
-            best = None
-            for plan in candidates(cap_log2):
-                dfr.check(dfr.dfr_tune_set(kt, c, plan), "tune_set")
-                case.time_ms(2)
-                ms = case.time_ms(reps)
-                if best is None or ms < best[0]:
-                    best = (ms, plan)
+            forms = (dfr.DFR_LAUNCH_LEVELS, dfr.DFR_LAUNCH_PERSISTENT) if (
+                both_forms and n * count < dfr.DFR_PERSIST_AUTO_KEYS) else (dfr.DFR_LAUNCH_AUTO,)
+            plans = candidates(cap_log2)
+            times = {}
+            for i, plan in enumerate(plans):
+                for form in forms:
+                    dfr.check(dfr.dfr_tune_set(kt, c, dict(plan, launch=form)), "tune_set")
+                    case.time_ms(2)
+                    times.setdefault(i, {})[form] = case.time_ms(reps)
+            i = pick_plan(times)
+            best = (sum(times[i].values()) / len(forms), plans[i])
             # The schedule of the top digits applies to single arrays large
             # enough for the LSD phase: tried on top of the best MSD plan.
             if count == 1 and n >= dfr.dfr_lsd_min_keys(kt):
@@ -173,6 +194,8 @@ def main(argv=None):
     ap.add_argument("--out-json", default="")
     ap.add_argument("--write-inc", action="store_true")
     ap.add_argument("--inc-path", default=INC)
+    ap.add_argument("--both-forms", action="store_true",
+                    help="time the classes that run as one persistent launch in both launch forms")
     ap.add_argument("--schedules", default="0,1",
                     help="schedules of the top digits to try on single large arrays (0 MSD, 1 LSD, 2 LSD with the "
                          "estimated deal, which falls back to MSD on skewed inputs and is left out by default)")
@@ -181,7 +204,7 @@ def main(argv=None):
         sys.path.insert(0, os.path.dirname(HERE))
     t0 = time.time()
     table = tune(args.key_types.split(","), [int(x) for x in args.classes.split(",")], args.reps, args.budget_keys,
-                 schedules=tuple(int(x) for x in args.schedules.split(",")))
+                 schedules=tuple(int(x) for x in args.schedules.split(",")), both_forms=args.both_forms)
     import torch
 
     meta = {"device": torch.cuda.get_device_name(0), "date": datetime.date.today().isoformat(),

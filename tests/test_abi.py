@@ -238,3 +238,19 @@ def test_lsd_minimum_and_size_classes(lib):
         assert dfr.dfr_tune_class(lo) == c and dfr.dfr_tune_class(hi - 1) == c and dfr.dfr_tune_class(hi) == c + 1
     assert dfr.dfr_tune_class((1 << 12) - 1) == 0
     assert dfr.dfr_tune_class(1 << 40) == dfr.DFR_TUNE_CLASSES - 1
+
+
+def test_tuner_picks_the_plan_balanced_over_launch_forms():
+    """tune.pick_plan keeps the plan with the smallest mean of its times
+    divided by each launch form's best time: a plan fastest in one form but
+    slow in the other loses to one close to the best in both."""
+    from paper_2207_14334_gb300 import tune
+
+    times = {
+        "fast_levels_only": {1: 1.00, 2: 2.00},  # 1.0 and 2.0 of the bests -> 1.5
+        "fast_persistent_only": {1: 1.60, 2: 1.00},  # 1.6 and 1.0 -> 1.3
+        "balanced": {1: 1.10, 2: 1.10},  # 1.1 and 1.1 -> 1.1
+    }
+    assert tune.pick_plan(times) == "balanced"
+    # one form only: the fastest plan
+    assert tune.pick_plan({"a": {0: 2.0}, "b": {0: 1.5}, "c": {0: 3.0}}) == "b"
